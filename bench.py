@@ -1,0 +1,376 @@
+"""Benchmark: earliest-arrival-time queries per second on one GB300 (and N replicas).
+
+Workload (default "city"): a 20,000-stop random geometric transit network (k = 4
+nearest neighbours, 400 routes of 30-60 stops run both ways, headways 5-20 min,
+20 % jittered trips, peak durations x1.3), about 3.6 M connections; one step =
+one batch of 256 queries (random source with departures, t_s uniform in
+05:00-22:00), all relaxation rounds of all queries in one launch.
+
+Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on the
+launching stream; L2 is flushed (a 256 MB buffer is written) before every step,
+outside the events; inputs are resident in device memory before timing starts.
+`e2e` repeats the measurement through the C ABI with pinned host buffers, so each
+step includes the host->device copy of the queries and the device->host copy of
+every arrival row.
+
+Roofline: algorithmic bytes per launch come from the kernel's own per-query work
+counters (stops expanded, types examined, AP records read, relaxations) times
+fixed per-unit byte figures; see the design doc for the figures.
+
+`--impl reference` times the CPU oracle (connection scan, Algorithm 1) on the host
+cores on the same queries instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+BATCH = 256
+FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+# Per-unit algorithmic bytes (the survey's figures): per expanded stop 8 B frontier
+# entry + 4 B e[u] + 8 B row offsets; per examined type 16 B type record; per type
+# that reads e[v] 4 B; per cluster lookup 8 B of cluster offsets; per AP record 16 B;
+# per successful relaxation 4 B atomic write + 8 B frontier push; per query 4 B x V
+# initialisation + 4 B x V result row.
+BYTES = {"vertices": 20, "types": 16, "evals": 4, "lookups": 8, "aps": 16, "relaxed": 12}
+
+# DRAM bytes per query of the CTA kernel on the city workload, from the ncu capture
+# summarised in profiles/; keyed by the kernel source hash so that a changed kernel
+# reports null until it is profiled again.
+NCU_TRAFFIC_PER_QUERY = {}
+
+
+def kernel_hash() -> str:
+    p = os.path.join(ROOT, "paper_1912_00966_gb300", "csrc", "eat_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def workload(name: str, seed_offset: int = 0):
+    if name == "city":
+        return synth.city(seed_offset=seed_offset), BATCH
+    if name == "small":
+        return synth.small_grid(seed_offset=seed_offset), BATCH
+    if name == "large":
+        return synth.large(seed_offset=seed_offset), 1024
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(name, tt, batch):
+    desc = {
+        "city": "city20k: 20,000-stop geometric k=4 network, 400 routes x2 directions of 30-60 "
+                "stops, headway 5-20 min, 20% jittered trips, 2 duration bands",
+        "small": "grid1024: 32x32 grid, 50 routes of 20 stops, headway 10-30 min",
+        "large": "large200k: 200,000-stop geometric k=5 network, 4,000 routes x2 of 40-80 "
+                 "stops, headway 3-30 min, 10% jittered trips, 3 duration bands",
+    }[name]
+    return {"workload": desc, "global_batch": batch, "n_stops": int(tt.n_stops),
+            "n_connections": int(tt.n_conn), "times": "int32 seconds",
+            "l2": "flushed before every step (256 MB write)", "parallelism": "replicas"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(tt, batches, budget_s, threads):
+    """Time the oracle on whole 256-query batches until about budget_s seconds pass."""
+    import oracle
+    sc = oracle.SortedConnections(tt)
+    done, t_used = 0, 0.0
+    used = threads
+    for src, ts in batches:
+        t0 = time.perf_counter()
+        _, used = oracle.csa_many(sc, src, ts, threads)
+        t_used += time.perf_counter() - t0
+        done += len(src)
+        if t_used >= budget_s:
+            break
+    return done / t_used, used, done, t_used
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    tt, batch = workload(args.workload)
+    batches = [(q.source, q.t_s) for q in
+               (synth.random_queries(tt, batch, 0xB0 + i) for i in range(args.warmup + args.steps))]
+    import oracle
+    sc = oracle.SortedConnections(tt)
+    threads = os.cpu_count() or 1
+    used = threads
+    for src, ts in batches[:args.warmup]:
+        oracle.csa_many(sc, src, ts, threads)
+    times = []
+    for src, ts in batches[args.warmup:]:
+        t0 = time.perf_counter()
+        _, used = oracle.csa_many(sc, src, ts, threads)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = batch * len(times) / total
+    line = {
+        "impl": "reference", "metric": "EAT queries/s (batched)", "value": value,
+        "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": describe(args.workload, tt, batch),
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": used, "kind": "oracle",
+                         "sample": f"every query of each {batch}-query step, connection scan "
+                                   f"(Algorithm 1) on {used} host threads"},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    from paper_1912_00966_gb300 import eat
+
+    tt, batch = workload(args.workload)
+    net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=dev)
+    st = eat.eat_get_stats(net)
+    V = tt.n_stops
+    n_steps = args.warmup + args.steps
+    qsets = [synth.random_queries(tt, batch, 0xB0 + 1000 * rank + i) for i in range(n_steps)]
+    src_d = [torch.as_tensor(q.source).cuda() for q in qsets]
+    ts_d = [torch.as_tensor(q.t_s).cuda() for q in qsets]
+    out = torch.empty(batch * V, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros((n_steps, batch, 7), dtype=torch.int64, device="cuda")
+    status = torch.zeros((n_steps, batch), dtype=torch.int32, device="cuda")
+    opts = dict(vwarp=args.vwarp, block=args.block)
+    ws = torch.empty(eat.eat_workspace_bytes(net, batch, **opts), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n_steps)]
+
+    def step(i):
+        flush.fill_(i)
+        a, b = evs[i]
+        a.record(stream)
+        eat.eat_query_batch(net, src_d[i], ts_d[i], out, workspace=ws, stream=stream,
+                            status=status[i], counters=cnt[i], **opts)
+        b.record(stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clocks:
+        t_wall = time.perf_counter()
+        for i in range(args.warmup, n_steps):
+            step(i)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(args.warmup, n_steps)]
+    gpu_s = sum(step_ms) / 1e3
+    if (status.cpu().numpy() != 0).any():
+        raise SystemExit("bench: a query did not converge")
+    c = cnt[args.warmup:].sum(dim=(0, 1)).cpu().numpy()
+    names = eat.COUNTER_FIELDS
+    tot = {n: int(c[k]) for k, n in enumerate(names)}
+    alg_bytes = sum(BYTES[n] * tot[n] for n in BYTES) + 8 * V * batch * args.steps
+    per_launch = alg_bytes / args.steps
+    mean_ms = gpu_s * 1e3 / args.steps
+
+    # The same queries end to end through the C ABI from pinned host buffers.
+    src_h = [torch.as_tensor(q.source).pin_memory() for q in qsets]
+    ts_h = [torch.as_tensor(q.t_s).pin_memory() for q in qsets]
+    out_h = torch.empty(batch * V, dtype=torch.int32).pin_memory()
+    for i in range(args.warmup):
+        eat.eat_query_batch(net, src_h[i], ts_h[i], out_h, stream=stream, **opts)
+    e2e_t = []
+    for i in range(args.warmup, n_steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eat.eat_query_batch(net, src_h[i], ts_h[i], out_h, stream=stream, **opts)
+        e2e_t.append(time.perf_counter() - t0)
+
+    # Plain single-query fixpoint (one blocking query at a time), for comparison.
+    plain_n = min(64, batch)
+    row = torch.empty(V, dtype=torch.int32, device="cuda")
+    q0 = qsets[-1]
+    for i in range(4):
+        eat.eat_query(net, int(q0.source[i]), int(q0.t_s[i]), row)
+    t0 = time.perf_counter()
+    for i in range(plain_n):
+        eat.eat_query(net, int(q0.source[i]), int(q0.t_s[i]), row)
+    plain_s = time.perf_counter() - t0
+
+    times = torch.tensor([gpu_s, sum(e2e_t), plain_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    gpu_s, e2e_s, plain_s = times.tolist()
+    if rank != 0:
+        return 0
+
+    peak, peak_kind = measured_peak()
+    achieved = per_launch / (mean_ms / 1e3) / 1e9
+    h = kernel_hash()
+    traffic = None
+    if args.workload in NCU_TRAFFIC_PER_QUERY and NCU_TRAFFIC_PER_QUERY[args.workload][0] == h:
+        traffic = NCU_TRAFFIC_PER_QUERY[args.workload][1] * batch
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, used, done, spent = cpu_oracle_rate(
+            tt, [(q.source, q.t_s) for q in qsets[args.warmup:]], args.cpu_budget, threads)
+        cpu = {"value": rate, "unit": "queries/s", "cores": used, "kind": "oracle",
+               "sample": f"{done} of the timed steps' queries ({done // batch} whole "
+                         f"{batch}-query batches), connection scan on {used} threads, "
+                         f"{spent:.1f} s"}
+
+    n_q = batch * args.steps * world
+    line = {
+        "metric": "EAT queries/s (batched)",
+        "value": n_q / gpu_s,
+        "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": gpu_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": describe(args.workload, tt, batch),
+        "e2e": {"value": n_q / e2e_s, "unit": "queries/s",
+                "h2d_bytes_per_step": 2 * 4 * batch, "d2h_bytes_per_step": 4 * V * batch},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} (burst copy)",
+                     "kernel": "eat_cta_kernel", "alg_bytes_per_launch": per_launch},
+        "cpu_baseline": cpu,
+        "connections_relaxed_per_s": tot["types"] / (gpu_s / world),
+        "plain_single_query": {"value": plain_n / plain_s, "unit": "queries/s",
+                               "ms_per_query": 1e3 * plain_s / plain_n},
+        "work_per_query": {n: tot[n] / (batch * args.steps) for n in names},
+        "network": {k: st[k] for k in ("n_types", "n_edges", "n_ap", "n_cl", "max_clusters",
+                                       "device_bytes")},
+        "clocks": clocks.summary(),
+        "kernel_hash": h,
+        "wall_s_timed_region": t_wall,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="city", choices=["city", "small", "large"])
+    ap.add_argument("--vwarp", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,265 @@
+/*
+ * eat.h -- C ABI of libeat: earliest-arrival-time (EAT) queries on public
+ * transport timetables, computed on one NVIDIA GB300 (sm_103a) GPU.
+ *
+ * Method: "GPU Algorithm for Earliest Arrival Time Problem in Public Transport
+ * Networks" (arXiv 1912.00966).
+ *   - Problem (Section I and Section II, Preliminaries): a connection
+ *     (u, v, t, lambda) leaves stop u at time t and reaches v at t + lambda.
+ *     For a query (s, t_s), e[v] is the earliest arrival at v over
+ *     time-respecting paths that leave s at or after t_s; e[s] = t_s.
+ *   - Data structure (Section IV-A): connections of one edge (u, v) with one
+ *     duration form a connection type (Section III-B); each type's departures
+ *     are split into clusters of `cluster_width` seconds (one hour in the
+ *     paper, Section III-D) and each cluster is stored as arithmetic
+ *     progressions (Section II, Arithmetic Progression Technique; Section III-C).
+ *   - Query (Algorithms 2, 3 and 5 with the Cluster-AP lookup of Section III-D,
+ *     the double-buffered activity of Section IV-B and atomicMin of Section
+ *     IV-C): rounds relax the connection types whose tail stop improved in the
+ *     previous round until no arrival changes.
+ *
+ * Conventions
+ *   - Times are int32 seconds.  EAT_INF (INT32_MAX) marks an unreachable stop.
+ *   - Stops are numbered 0 .. n_stops-1.
+ *   - Every function returns EAT_OK (0) or one of the EAT_ERR_* codes;
+ *     eat_last_error() returns a message for the calling thread's last error.
+ *   - "device memory" means memory of the network's CUDA device (cudaMalloc,
+ *     torch CUDA tensors); "host memory" is ordinary or pinned CPU memory.
+ *     Entry points that accept either detect the kind with
+ *     cudaPointerGetAttributes.
+ *   - Streams are passed as `void *` holding a cudaStream_t (NULL = the
+ *     legacy default stream).
+ */
+#ifndef EAT_H
+#define EAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EAT_INF INT32_MAX
+
+enum eat_status {
+    EAT_OK = 0,
+    EAT_ERR_INVALID = 1,        /* bad argument or input data (message says which) */
+    EAT_ERR_OOM = 2,            /* host or device allocation failed */
+    EAT_ERR_CUDA = 3,           /* a CUDA runtime call failed (message has the CUDA error) */
+    EAT_ERR_NO_CONVERGENCE = 4, /* a query hit its round cap before the fixpoint */
+    EAT_ERR_NO_DEVICE = 5,      /* the network was built host-only, or no CUDA device */
+    EAT_ERR_WORKSPACE = 6       /* the caller's workspace is smaller than required */
+};
+
+/* Opaque network: built once, immutable afterwards, resident on one GPU. */
+typedef struct eat_net eat_net;
+
+/* Input timetable: n_conn connections as four parallel int32 arrays in host
+ * memory (Section II, Preliminaries).  Requirements, checked by eat_build:
+ * 0 <= u, v < n_stops; dur >= 1; dep >= t0 (see eat_build_opts);
+ * dep + dur < INT32_MAX.  Identical connections are merged. */
+typedef struct {
+    int32_t n_stops;
+    int64_t n_conn;
+    const int32_t *u;
+    const int32_t *v;
+    const int32_t *dep;
+    const int32_t *dur;
+} eat_connections;
+
+/* Build options.  Zero-initialise for the paper's defaults. */
+typedef struct {
+    int32_t cluster_width; /* seconds per cluster, 1..65535; 0 = 3600 (Section III-D) */
+    int32_t t0;            /* start of cluster 0; departures must be >= t0; default 0 */
+    int32_t device;        /* CUDA device ordinal; -1 = host-only build (inspection only) */
+    int32_t reserved;
+} eat_build_opts;
+
+/* Sizes of a built network. */
+typedef struct {
+    int32_t n_stops;
+    int32_t n_types;        /* connection types C_{u,v,lambda} (Section III-B) */
+    int32_t n_edges;        /* distinct (u, v) pairs with connections */
+    int32_t cluster_width;
+    int32_t t0;
+    int32_t max_clusters;   /* y of Section IV-A: clusters spanned by the widest type */
+    int32_t max_out_types;  /* largest number of types leaving one stop */
+    int32_t device;         /* -1 for a host-only build */
+    int64_t n_conn;         /* connections after merging identical ones */
+    int64_t n_ap;           /* AP records */
+    int64_t n_cl;           /* cluster-offset entries */
+    int64_t device_bytes;   /* bytes of the resident device copy */
+} eat_stats;
+
+/* Read-only host view of the built arrays (Section IV-A's CT[], CL[], AP[], in
+ * this library's layout).  Valid until eat_free.
+ *   row_ptr [n_stops + 1]: types leaving stop u are row_ptr[u] .. row_ptr[u+1]-1,
+ *                          ordered by (v, lambda).
+ *   type_rec[4 * n_types]: per type {v, lambda, first departure, last departure}.
+ *   type_cl [n_types]:     cl_base; the APs of cluster k of the type are
+ *                          ap[cl[cl_base + k]] .. ap[cl[cl_base + k + 1] - 1] for the
+ *                          clusters k between the type's first and last departure;
+ *                          a type's APs are contiguous and ordered by cluster, then
+ *                          by first term.
+ *   cl      [n_cl]
+ *   ap      [2 * n_ap]:    per AP {first term, (difference << 16) | number of terms};
+ *                          a one-term AP has difference 0. */
+typedef struct {
+    const int32_t *row_ptr;
+    const int32_t *type_rec;
+    const int32_t *type_cl;
+    const int32_t *cl;
+    const uint32_t *ap;
+} eat_net_view;
+
+/* Per-query work counters (optional output of the query calls). */
+typedef struct {
+    int64_t rounds;    /* relaxation rounds run (Algorithm 5's while loop) */
+    int64_t vertices;  /* active stops expanded, summed over rounds */
+    int64_t types;     /* connection types examined with an active tail: the
+                          "connections processed" of Section V-C */
+    int64_t evals;     /* of those, types with a departure at or after e[u]
+                          (their e[v] is read) */
+    int64_t lookups;   /* of those, types whose cluster was searched (Section III-D) */
+    int64_t aps;       /* AP records read by the cluster lookup (Algorithm 6) */
+    int64_t relaxed;   /* successful lowerings of some e[v] (Algorithm 3) */
+} eat_counters;
+
+/* Query options.  Zero-initialise for defaults. */
+typedef struct {
+    int32_t max_rounds;      /* round cap; 0 = n_stops + 1 (always enough: every
+                                productive round fixes at least one more stop) */
+    int32_t block;           /* threads per CTA: 0 = automatic, else 64..1024, multiple of 32 */
+    int32_t vwarp;           /* lanes per active stop (1, 2, 4, 8, 16 or 32); 0 = automatic */
+    int32_t mode;            /* EAT_MODE_* */
+    int32_t placement;       /* EAT_PLACE_*: where a query's arrivals and frontier
+                                bitmap live; 0 = automatic */
+    int32_t reserved;
+    int32_t *status;         /* optional [n] per-query eat_status, device memory */
+    eat_counters *counters;  /* optional [n] per-query counters, device memory */
+} eat_query_opts;
+
+enum eat_placement {
+    EAT_PLACE_AUTO = 0,
+    EAT_PLACE_SHARED = 1,        /* arrivals and bitmap in shared memory (needs
+                                    4 * n_stops + n_stops / 8 bytes to fit a CTA) */
+    EAT_PLACE_GLOBAL_ARR = 2,    /* arrivals in the output row, bitmap in shared memory */
+    EAT_PLACE_GLOBAL = 3         /* arrivals and bitmap in global memory */
+};
+
+enum eat_mode {
+    EAT_MODE_AUTO = 0,  /* library picks */
+    EAT_MODE_CTA = 1,   /* one thread block per query; rounds end at block barriers */
+    EAT_MODE_GRID = 2   /* all SMs on each round of one query at a time */
+};
+
+/* Error message of the calling thread's last failed call ("" if none). */
+const char *eat_last_error(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int32_t eat_version(void);
+
+/*
+ * eat_build -- preprocess a timetable into the Cluster-AP layout and upload it.
+ * Section IV-A (graph representation and preprocessing): group connections by
+ * edge and duration into connection types (Section III-B), split each type by
+ * departure time into clusters of cluster_width seconds (Section III-D), cover
+ * each cluster by the greedy AP cover (Section II; Section III-C), order the
+ * APs of a cluster by first term.
+ *   conn  host arrays, read only during the call (copied).
+ *   opts  may be NULL (defaults).
+ *   out   receives a new network owned by the caller; release with eat_free.
+ * Errors: EAT_ERR_INVALID (bad sizes, ids, durations, times or options),
+ * EAT_ERR_OOM, EAT_ERR_CUDA, EAT_ERR_NO_DEVICE.  On error *out is NULL.
+ */
+int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net **out);
+
+/* Release a network and its device memory.  NULL is ignored.  No query on the
+ * network may be in flight. */
+void eat_free(eat_net *net);
+
+/* Sizes of a network.  Errors: EAT_ERR_INVALID on NULL arguments. */
+int eat_get_stats(const eat_net *net, eat_stats *out);
+
+/* Host view of the built arrays (see eat_net_view).  Works for host-only builds. */
+int eat_net_host_view(const eat_net *net, eat_net_view *out);
+
+/*
+ * eat_query -- one query (s, t_s), blocking (Algorithms 2-5, Section III-D).
+ *   arr_out  [n_stops] int32, host or device memory: arr_out[v] = e[v],
+ *            EAT_INF if v is unreachable; arr_out[s] = t_s.
+ *   counters optional (NULL), host memory.
+ * Runs on the legacy default stream with the network's own workspace, so
+ * concurrent eat_query calls on one network are serialised internally.
+ * Errors: EAT_ERR_INVALID (s out of range, NULL arr_out), EAT_ERR_NO_DEVICE,
+ * EAT_ERR_NO_CONVERGENCE (round cap hit; arr_out then holds upper bounds),
+ * EAT_ERR_CUDA.
+ */
+int eat_query(const eat_net *net, int32_t s, int32_t t_s, int32_t *arr_out,
+              eat_counters *counters);
+
+/*
+ * eat_workspace_bytes -- device workspace needed by eat_query_batch(_multi) for
+ * n queries over the given networks with these options (opts may be NULL).
+ * Returns 0 on invalid arguments.
+ */
+size_t eat_workspace_bytes(const eat_net *const *nets, int32_t n_nets, int32_t n,
+                           const eat_query_opts *opts);
+
+/*
+ * eat_query_batch -- n independent queries (sources[i], times[i]) on one
+ * network, in one launch (batching across queries is this library's addition;
+ * each query follows the same algorithm as eat_query).
+ *   sources, times  [n] int32, host or device memory.
+ *   arr_out         [n * n_stops] int32 row-major (row i = query i), host or
+ *                   device memory.
+ *   workspace       device memory of at least eat_workspace_bytes(&net, 1, n, opts)
+ *                   bytes, or NULL to use the network's internal workspace (then
+ *                   calls on one network must not overlap).
+ *   opts            may be NULL.
+ *   stream          cudaStream_t to run on.
+ * If every buffer is device memory the call is asynchronous on `stream`.  If
+ * any is host memory the call stages through device memory and returns after
+ * the results are in arr_out.  Per-query round-cap failures are reported
+ * only through opts->status (the return value covers launch errors).
+ * Errors: EAT_ERR_INVALID, EAT_ERR_WORKSPACE, EAT_ERR_NO_DEVICE, EAT_ERR_CUDA,
+ * EAT_ERR_OOM.
+ */
+int eat_query_batch(const eat_net *net, const int32_t *sources, const int32_t *times,
+                    int32_t n, int32_t *arr_out, void *workspace, size_t workspace_bytes,
+                    const eat_query_opts *opts, void *stream);
+
+/*
+ * eat_query_batch_multi -- n queries over several networks of uneven size in
+ * one launch.  Query i runs on nets[net_idx[i]] and writes its
+ * nets[net_idx[i]]->n_stops arrivals at arr_out + arr_offsets[i].
+ *   nets         [n_nets] host array of networks, all on the same device,
+ *                1 <= n_nets <= EAT_MAX_NETS.
+ *   net_idx, sources, times  [n] int32; arr_offsets [n] int64 (element offsets);
+ *                host or device memory, all of the same kind.
+ *   arr_out      device memory large enough for every row.
+ * Asynchronous on `stream`.  Other arguments as eat_query_batch.
+ */
+#define EAT_MAX_NETS 128
+int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int32_t *net_idx,
+                          const int32_t *sources, const int32_t *times, int32_t n,
+                          int32_t *arr_out, const int64_t *arr_offsets, void *workspace,
+                          size_t workspace_bytes, const eat_query_opts *opts, void *stream);
+
+/*
+ * eat_next_departure -- the Cluster-AP lookup alone (getConnection with
+ * getConnectionFromAPs, Algorithm 6, inside the hourly cluster of Section
+ * III-D): for each i, out[i] = least departure >= times[i] of connection type
+ * types[i], or EAT_INF if there is none.  Exposes the kernel's lookup for
+ * testing.  types, times, out: [n] int32 device memory.  Asynchronous on stream.
+ * Errors: EAT_ERR_INVALID (type index out of range), EAT_ERR_NO_DEVICE,
+ * EAT_ERR_CUDA.
+ */
+int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *times,
+                       int32_t n, int32_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EAT_H */

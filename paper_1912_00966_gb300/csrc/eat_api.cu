@@ -1,0 +1,553 @@
+// C ABI of libeat (declared in include/eat.h): build, free, inspection, queries.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "eat_internal.h"
+
+#include "eat_launch.h"
+
+namespace eat {
+
+static thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+void clear_error() { g_err.clear(); }
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    return fail(EAT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Restores the calling thread's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------------------ launch planning
+
+struct DeviceInfo {
+    int sms = 0;
+    size_t smem_optin = 0;
+    size_t smem_static_reserve = 1024;  // static __shared__ of the kernel + margin
+    bool init = false;
+};
+
+static std::mutex g_dev_lock;
+static DeviceInfo g_dev[64];
+
+static int device_info(int dev, DeviceInfo &out) {
+    if (dev < 0 || dev >= 64) return fail(EAT_ERR_INVALID, "device ordinal out of range");
+    std::lock_guard<std::mutex> g(g_dev_lock);
+    DeviceInfo &d = g_dev[dev];
+    if (!d.init) {
+        int v = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(SM count)");
+        d.sms = v;
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(smem optin)");
+        d.smem_optin = (size_t)v;
+        // Allow every CTA kernel the full opt-in shared memory (once per device).
+        DeviceGuard guard(dev);
+        for (int nets : {1, EAT_MAX_NETS})
+            for (int mem = 0; mem < 3; ++mem) {
+                e = cudaFuncSetAttribute(cta_kernel(nets, mem),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(d.smem_optin - d.smem_static_reserve));
+                if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+            }
+        d.init = true;
+    }
+    out = d;
+    return EAT_OK;
+}
+
+struct Plan {
+    int mem = 0;
+    int block = 512;
+    int vw_log2 = 3;
+    int grid = 0;
+    size_t smem = 0;
+    int32_t vmax = 0;
+    int64_t queue_stride = 0;
+    int64_t mask_stride = 0;
+    size_t ws_bytes = 0;
+    size_t off_queues = 0, off_mask = 0;
+    int nets = 1;
+};
+
+static constexpr size_t kWsHeader = 256;   // work counter + internal status / counters
+
+static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_query_opts *o,
+                     Plan &p) {
+    DeviceInfo d;
+    int rc = device_info(dev, d);
+    if (rc) return rc;
+    p.nets = n_nets == 1 ? 1 : EAT_MAX_NETS;
+    p.vmax = vmax;
+    p.block = (o && o->block) ? o->block : 512;
+    if (p.block < 64 || p.block > 1024 || p.block % 32)
+        return fail(EAT_ERR_INVALID, "block must be a multiple of 32 in 64..1024");
+    int vw = (o && o->vwarp) ? o->vwarp : 8;
+    int l = 0;
+    while ((1 << l) < vw) ++l;
+    if ((1 << l) != vw || vw > 32) return fail(EAT_ERR_INVALID, "vwarp must be 1, 2, 4, 8, 16 or 32");
+    p.vw_log2 = l;
+    const size_t words = ((size_t)vmax + 31) / 32;
+    const size_t arr_bytes = align_up((size_t)vmax, 4) * 4 + words * 4;
+    const size_t limit = d.smem_optin - d.smem_static_reserve;
+    const int place = o ? o->placement : EAT_PLACE_AUTO;
+    if (place < EAT_PLACE_AUTO || place > EAT_PLACE_GLOBAL)
+        return fail(EAT_ERR_INVALID, "placement must be one of EAT_PLACE_*");
+    if (o && o->mode != EAT_MODE_AUTO && o->mode != EAT_MODE_CTA)
+        return fail(EAT_ERR_INVALID, "mode must be EAT_MODE_AUTO or EAT_MODE_CTA");
+    if (place == EAT_PLACE_SHARED && arr_bytes > limit)
+        return fail(EAT_ERR_INVALID, "arrivals do not fit in shared memory");
+    if (place == EAT_PLACE_GLOBAL_ARR && words * 4 > limit)
+        return fail(EAT_ERR_INVALID, "bitmap does not fit in shared memory");
+    if (place == EAT_PLACE_SHARED || (place == EAT_PLACE_AUTO && arr_bytes <= limit)) {
+        p.mem = 0;
+        p.smem = arr_bytes;
+    } else if (place == EAT_PLACE_GLOBAL_ARR || (place == EAT_PLACE_AUTO && words * 4 <= limit)) {
+        p.mem = 1;
+        p.smem = words * 4;
+    } else {
+        p.mem = 2;
+        p.smem = 0;
+    }
+    int per_sm = 0;
+    cudaError_t e;
+    {
+        DeviceGuard guard(dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cta_kernel(p.nets, p.mem),
+                                                          p.block, p.smem);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) return fail(EAT_ERR_INVALID, "kernel does not fit on an SM with this block size");
+    p.grid = (int)std::min<int64_t>((int64_t)std::max(n, 1), (int64_t)per_sm * d.sms);
+    p.queue_stride = (int64_t)align_up((size_t)vmax * 2, 64);
+    p.mask_stride = p.mem == 2 ? (int64_t)align_up(words, 64) : 0;
+    p.off_queues = kWsHeader;
+    p.off_mask = p.off_queues + (size_t)p.grid * (size_t)p.queue_stride * 4;
+    p.ws_bytes = p.off_mask + (size_t)p.grid * (size_t)p.mask_stride * 4;
+    return EAT_OK;
+}
+
+static int ensure_buffer(void *&buf, size_t &cap, size_t need) {
+    if (cap >= need) return EAT_OK;
+    if (buf) cudaFree(buf);
+    buf = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&buf, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EAT_ERR_OOM, "cudaMalloc of " + std::to_string(need) + " bytes failed");
+    }
+    cap = need;
+    return EAT_OK;
+}
+
+// Runs a batch whose buffers are all device memory.
+static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_idx,
+                     const int32_t *src, const int32_t *ts, int32_t n, int32_t *arr_out,
+                     const int64_t *arr_off, void *ws, size_t ws_bytes,
+                     const eat_query_opts *o, cudaStream_t st, int32_t *status_override,
+                     eat_counters *counters_override) {
+    const int dev = nets[0]->device;
+    int32_t vmax = 0;
+    for (int i = 0; i < n_nets; ++i) vmax = std::max(vmax, nets[i]->host.n_stops);
+    Plan p;
+    int rc = make_plan(dev, vmax, n, n_nets, o, p);
+    if (rc) return rc;
+    if (ws_bytes < p.ws_bytes)
+        return fail(EAT_ERR_WORKSPACE, "workspace of " + std::to_string(ws_bytes) +
+                                           " bytes, need " + std::to_string(p.ws_bytes));
+    if (n == 0) return EAT_OK;
+    char *w = (char *)ws;
+    QueryArgs qa;
+    qa.net_idx = net_idx;
+    qa.src = src;
+    qa.ts = ts;
+    qa.arr_off = arr_off;
+    qa.arr_out = arr_out;
+    qa.queues = (int32_t *)(w + p.off_queues);
+    qa.gmask = (uint32_t *)(w + p.off_mask);
+    qa.work = (int32_t *)w;
+    qa.status = status_override ? status_override : (o ? o->status : nullptr);
+    qa.counters = counters_override ? counters_override : (o ? o->counters : nullptr);
+    qa.queue_stride = p.queue_stride;
+    qa.mask_stride = p.mask_stride;
+    qa.n = n;
+    qa.n_nets = n_nets;
+    int32_t cap = (o && o->max_rounds > 0) ? o->max_rounds : (vmax < INT32_MAX ? vmax + 1 : vmax);
+    qa.max_rounds = cap;
+    qa.vw_log2 = p.vw_log2;
+    DeviceGuard guard(dev);
+    cudaError_t e = cudaMemsetAsync(qa.work, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    NetDev devs[EAT_MAX_NETS];
+    for (int i = 0; i < n_nets; ++i) devs[i] = nets[i]->dev;
+    e = launch_cta(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "CTA kernel launch");
+    return EAT_OK;
+}
+
+}  // namespace eat
+
+using namespace eat;
+
+extern "C" {
+
+const char *eat_last_error(void) { return g_err.c_str(); }
+
+int32_t eat_version(void) { return 100; }
+
+int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net **out) {
+    clear_error();
+    if (!out) return fail(EAT_ERR_INVALID, "out must not be NULL");
+    *out = nullptr;
+    if (!conn) return fail(EAT_ERR_INVALID, "conn must not be NULL");
+    eat_build_opts o{};
+    if (opts) o = *opts;
+    const int32_t width = o.cluster_width ? o.cluster_width : 3600;
+    eat_net *net = new (std::nothrow) eat_net();
+    if (!net) return fail(EAT_ERR_OOM, "host allocation failed");
+    int rc = build_host(conn, width, o.t0, net->host);
+    if (rc) {
+        delete net;
+        return rc;
+    }
+    net->device = o.device;
+    if (o.device >= 0) {
+        int count = 0;
+        cudaError_t e = cudaGetDeviceCount(&count);
+        if (e != cudaSuccess || o.device >= count) {
+            cudaGetLastError();
+            delete net;
+            return fail(EAT_ERR_NO_DEVICE, "no CUDA device " + std::to_string(o.device));
+        }
+        const HostNet &h = net->host;
+        size_t off_row = 0;
+        size_t off_ty = align_up(off_row + ((size_t)h.n_stops + 1) * 4, 256);
+        size_t off_clb = align_up(off_ty + (size_t)h.n_types * 16, 256);
+        size_t off_cl = align_up(off_clb + (size_t)h.n_types * 4, 256);
+        size_t off_ap = align_up(off_cl + h.cl.size() * 4, 256);
+        // One spare AP-sized word pair so that no read can run past the blob.
+        size_t total = align_up(off_ap + h.ap.size() * 4 + 16, 256);
+        DeviceGuard guard(o.device);
+        if (!guard.ok) {
+            delete net;
+            return fail(EAT_ERR_NO_DEVICE, "cudaSetDevice failed");
+        }
+        e = cudaMalloc(&net->blob, total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete net;
+            return fail(EAT_ERR_OOM, "cudaMalloc of the network failed");
+        }
+        net->blob_bytes = (int64_t)total;
+        char *b = (char *)net->blob;
+        struct Piece { size_t off; const void *src; size_t bytes; } pieces[] = {
+            {off_row, h.row_ptr.data(), h.row_ptr.size() * 4},
+            {off_ty, h.type_rec.data(), h.type_rec.size() * 4},
+            {off_clb, h.type_cl.data(), h.type_cl.size() * 4},
+            {off_cl, h.cl.data(), h.cl.size() * 4},
+            {off_ap, h.ap.data(), h.ap.size() * 4},
+        };
+        for (const Piece &pc : pieces) {
+            if (!pc.bytes) continue;
+            e = cudaMemcpy(b + pc.off, pc.src, pc.bytes, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(net->blob);
+                delete net;
+                return cuda_fail(e, "cudaMemcpy of the network");
+            }
+        }
+        NetDev &d = net->dev;
+        d.row_ptr = (const int32_t *)(b + off_row);
+        d.ty = (const int4 *)(b + off_ty);
+        d.cl_base = (const int32_t *)(b + off_clb);
+        d.cl = (const int32_t *)(b + off_cl);
+        d.ap = (const uint2 *)(b + off_ap);
+        d.n_stops = h.n_stops;
+        d.n_types = h.n_types;
+        d.t0 = h.t0;
+        d.width = h.width;
+    }
+    *out = net;
+    return EAT_OK;
+}
+
+void eat_free(eat_net *net) {
+    if (!net) return;
+    if (net->device >= 0) {
+        DeviceGuard guard(net->device);
+        if (net->blob) cudaFree(net->blob);
+        if (net->ws) cudaFree(net->ws);
+        if (net->stage) cudaFree(net->stage);
+    }
+    delete net;
+}
+
+int eat_get_stats(const eat_net *net, eat_stats *out) {
+    clear_error();
+    if (!net || !out) return fail(EAT_ERR_INVALID, "NULL argument");
+    const HostNet &h = net->host;
+    out->n_stops = h.n_stops;
+    out->n_types = h.n_types;
+    out->n_edges = h.n_edges;
+    out->cluster_width = h.width;
+    out->t0 = h.t0;
+    out->max_clusters = h.max_clusters;
+    out->max_out_types = h.max_out_types;
+    out->device = net->device;
+    out->n_conn = h.n_conn;
+    out->n_ap = (int64_t)h.ap.size() / 2;
+    out->n_cl = (int64_t)h.cl.size();
+    out->device_bytes = net->blob_bytes;
+    return EAT_OK;
+}
+
+int eat_net_host_view(const eat_net *net, eat_net_view *out) {
+    clear_error();
+    if (!net || !out) return fail(EAT_ERR_INVALID, "NULL argument");
+    out->row_ptr = net->host.row_ptr.data();
+    out->type_rec = net->host.type_rec.data();
+    out->type_cl = net->host.type_cl.data();
+    out->cl = net->host.cl.data();
+    out->ap = net->host.ap.data();
+    return EAT_OK;
+}
+
+size_t eat_workspace_bytes(const eat_net *const *nets, int32_t n_nets, int32_t n,
+                           const eat_query_opts *opts) {
+    clear_error();
+    if (!nets || n_nets < 1 || n_nets > EAT_MAX_NETS || n < 0) return 0;
+    int32_t vmax = 0;
+    for (int i = 0; i < n_nets; ++i) {
+        if (!nets[i] || nets[i]->device < 0 || nets[i]->device != nets[0]->device) return 0;
+        vmax = std::max(vmax, nets[i]->host.n_stops);
+    }
+    Plan p;
+    if (make_plan(nets[0]->device, vmax, n, n_nets, opts, p)) return 0;
+    return p.ws_bytes;
+}
+
+int eat_query(const eat_net *net, int32_t s, int32_t t_s, int32_t *arr_out,
+              eat_counters *counters) {
+    clear_error();
+    if (!net || !arr_out) return fail(EAT_ERR_INVALID, "NULL argument");
+    if (net->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
+    if (s < 0 || s >= net->host.n_stops) return fail(EAT_ERR_INVALID, "source out of range");
+    std::lock_guard<std::mutex> g(net->ws_lock);
+    Plan p;
+    int rc = make_plan(net->device, net->host.n_stops, 1, 1, nullptr, p);
+    if (rc) return rc;
+    DeviceGuard guard(net->device);
+    const bool dev_out = is_device_ptr(arr_out);
+    const size_t rows = dev_out ? 0 : align_up((size_t)net->host.n_stops * 4, 256);
+    rc = ensure_buffer(net->ws, net->ws_bytes, p.ws_bytes + rows + 256);
+    if (rc) return rc;
+    char *w = (char *)net->ws;
+    // Internal scratch after the plan's workspace: [src, t_s, status, pad][counters][row].
+    int32_t *io = (int32_t *)(w + p.ws_bytes);
+    eat_counters *cnt = (eat_counters *)(w + p.ws_bytes + 64);
+    int32_t *row = dev_out ? arr_out : (int32_t *)(w + p.ws_bytes + 256);
+    int32_t h_io[2] = {s, t_s};
+    cudaError_t e = cudaMemcpyAsync(io, h_io, sizeof(h_io), cudaMemcpyHostToDevice, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    const eat_net *nets[1] = {net};
+    rc = run_batch(nets, 1, nullptr, io, io + 1, 1, row, nullptr, w, p.ws_bytes, nullptr, 0,
+                   io + 2, cnt);
+    if (rc) return rc;
+    int32_t st_h = 0;
+    e = cudaMemcpyAsync(&st_h, io + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, 0);
+    if (e == cudaSuccess && counters)
+        e = cudaMemcpyAsync(counters, cnt, sizeof(eat_counters), cudaMemcpyDeviceToHost, 0);
+    if (e == cudaSuccess && !dev_out)
+        e = cudaMemcpyAsync(arr_out, row, (size_t)net->host.n_stops * 4, cudaMemcpyDeviceToHost, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return cuda_fail(e, "eat_query");
+    if (st_h == EAT_ERR_NO_CONVERGENCE) return fail(st_h, "round cap reached");
+    if (st_h) return fail(st_h, "query failed");
+    return EAT_OK;
+}
+
+int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int32_t *net_idx,
+                          const int32_t *sources, const int32_t *times, int32_t n,
+                          int32_t *arr_out, const int64_t *arr_offsets, void *workspace,
+                          size_t workspace_bytes, const eat_query_opts *opts, void *stream) {
+    clear_error();
+    if (!nets || n_nets < 1 || n_nets > EAT_MAX_NETS) return fail(EAT_ERR_INVALID, "bad nets");
+    for (int i = 0; i < n_nets; ++i) {
+        if (!nets[i]) return fail(EAT_ERR_INVALID, "NULL network");
+        if (nets[i]->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
+        if (nets[i]->device != nets[0]->device)
+            return fail(EAT_ERR_INVALID, "all networks must be on one device");
+    }
+    if (n < 0) return fail(EAT_ERR_INVALID, "n must be >= 0");
+    if (n > 0 && (!net_idx || !sources || !times || !arr_out || !arr_offsets))
+        return fail(EAT_ERR_INVALID, "NULL query array");
+    if (n > 0 && !is_device_ptr(arr_out)) return fail(EAT_ERR_INVALID, "arr_out must be device memory");
+    DeviceGuard guard(nets[0]->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dev_in = n == 0 || is_device_ptr(sources);
+    if (n > 0 && (is_device_ptr(net_idx) != dev_in || is_device_ptr(times) != dev_in ||
+                  is_device_ptr(arr_offsets) != dev_in))
+        return fail(EAT_ERR_INVALID, "query arrays must all be host or all device memory");
+    if (dev_in) {
+        if (!workspace) {
+            std::lock_guard<std::mutex> g(nets[0]->ws_lock);
+            size_t need = eat_workspace_bytes(nets, n_nets, n, opts);
+            if (!need) return EAT_ERR_INVALID;
+            int rc = ensure_buffer(nets[0]->ws, nets[0]->ws_bytes, need);
+            if (rc) return rc;
+            return run_batch(nets, n_nets, net_idx, sources, times, n, arr_out, arr_offsets,
+                             nets[0]->ws, nets[0]->ws_bytes, opts, st, nullptr, nullptr);
+        }
+        return run_batch(nets, n_nets, net_idx, sources, times, n, arr_out, arr_offsets, workspace,
+                         workspace_bytes, opts, st, nullptr, nullptr);
+    }
+    // Host query arrays: validate here, stage them through device memory.
+    for (int32_t i = 0; i < n; ++i) {
+        if (net_idx[i] < 0 || net_idx[i] >= n_nets) return fail(EAT_ERR_INVALID, "net_idx out of range");
+        if (sources[i] < 0 || sources[i] >= nets[net_idx[i]]->host.n_stops)
+            return fail(EAT_ERR_INVALID, "source out of range");
+    }
+    std::lock_guard<std::mutex> g(nets[0]->ws_lock);
+    const size_t in_bytes = align_up((size_t)n * 4, 256) * 3 + align_up((size_t)n * 8, 256);
+    int rc = ensure_buffer(nets[0]->stage, nets[0]->stage_bytes, in_bytes);
+    if (rc) return rc;
+    char *sb = (char *)nets[0]->stage;
+    int32_t *d_idx = (int32_t *)sb;
+    int32_t *d_src = (int32_t *)(sb + align_up((size_t)n * 4, 256));
+    int32_t *d_ts = (int32_t *)(sb + 2 * align_up((size_t)n * 4, 256));
+    int64_t *d_off = (int64_t *)(sb + 3 * align_up((size_t)n * 4, 256));
+    cudaError_t e = cudaMemcpyAsync(d_idx, net_idx, (size_t)n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_src, sources, (size_t)n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ts, times, (size_t)n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, arr_offsets, (size_t)n * 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    void *ws = workspace;
+    size_t wsb = workspace_bytes;
+    if (!ws) {
+        size_t need = eat_workspace_bytes(nets, n_nets, n, opts);
+        if (!need) return EAT_ERR_INVALID;
+        rc = ensure_buffer(nets[0]->ws, nets[0]->ws_bytes, need);
+        if (rc) return rc;
+        ws = nets[0]->ws;
+        wsb = nets[0]->ws_bytes;
+    }
+    rc = run_batch(nets, n_nets, d_idx, d_src, d_ts, n, arr_out, d_off, ws, wsb, opts, st,
+                   nullptr, nullptr);
+    if (rc) return rc;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return EAT_OK;
+}
+
+int eat_query_batch(const eat_net *net, const int32_t *sources, const int32_t *times, int32_t n,
+                    int32_t *arr_out, void *workspace, size_t workspace_bytes,
+                    const eat_query_opts *opts, void *stream) {
+    clear_error();
+    if (!net) return fail(EAT_ERR_INVALID, "NULL network");
+    if (net->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
+    if (n < 0) return fail(EAT_ERR_INVALID, "n must be >= 0");
+    if (n == 0) return EAT_OK;
+    if (!sources || !times || !arr_out) return fail(EAT_ERR_INVALID, "NULL query array");
+    DeviceGuard guard(net->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool d_src = is_device_ptr(sources), d_ts = is_device_ptr(times), d_out = is_device_ptr(arr_out);
+    const eat_net *nets[1] = {net};
+    if (d_src && d_ts && d_out) {
+        if (!workspace) {
+            std::lock_guard<std::mutex> g(net->ws_lock);
+            size_t need = eat_workspace_bytes(nets, 1, n, opts);
+            if (!need) return EAT_ERR_INVALID;
+            int rc = ensure_buffer(net->ws, net->ws_bytes, need);
+            if (rc) return rc;
+            return run_batch(nets, 1, nullptr, sources, times, n, arr_out, nullptr, net->ws,
+                             net->ws_bytes, opts, st, nullptr, nullptr);
+        }
+        return run_batch(nets, 1, nullptr, sources, times, n, arr_out, nullptr, workspace,
+                         workspace_bytes, opts, st, nullptr, nullptr);
+    }
+    // At least one host buffer: stage through device memory, then synchronise.
+    if (!d_src)
+        for (int32_t i = 0; i < n; ++i)
+            if (sources[i] < 0 || sources[i] >= net->host.n_stops)
+                return fail(EAT_ERR_INVALID, "source out of range");
+    std::lock_guard<std::mutex> g(net->ws_lock);
+    const size_t in_bytes = align_up((size_t)n * 4, 256);
+    const size_t out_bytes = (size_t)n * (size_t)net->host.n_stops * 4;
+    int rc = ensure_buffer(net->stage, net->stage_bytes, 2 * in_bytes + (d_out ? 0 : out_bytes));
+    if (rc) return rc;
+    char *sb = (char *)net->stage;
+    const int32_t *src_d = d_src ? sources : (const int32_t *)sb;
+    const int32_t *ts_d = d_ts ? times : (const int32_t *)(sb + in_bytes);
+    int32_t *out_d = d_out ? arr_out : (int32_t *)(sb + 2 * in_bytes);
+    cudaError_t e = cudaSuccess;
+    if (!d_src) e = cudaMemcpyAsync((void *)src_d, sources, (size_t)n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !d_ts)
+        e = cudaMemcpyAsync((void *)ts_d, times, (size_t)n * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    void *ws = workspace;
+    size_t wsb = workspace_bytes;
+    if (!ws) {
+        size_t need = eat_workspace_bytes(nets, 1, n, opts);
+        if (!need) return EAT_ERR_INVALID;
+        rc = ensure_buffer(net->ws, net->ws_bytes, need);
+        if (rc) return rc;
+        ws = net->ws;
+        wsb = net->ws_bytes;
+    }
+    rc = run_batch(nets, 1, nullptr, src_d, ts_d, n, out_d, nullptr, ws, wsb, opts, st, nullptr,
+                   nullptr);
+    if (rc) return rc;
+    if (!d_out) e = cudaMemcpyAsync(arr_out, out_d, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "eat_query_batch");
+    return EAT_OK;
+}
+
+int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *times, int32_t n,
+                       int32_t *out, void *stream) {
+    clear_error();
+    if (!net) return fail(EAT_ERR_INVALID, "NULL network");
+    if (net->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
+    if (n < 0) return fail(EAT_ERR_INVALID, "n must be >= 0");
+    if (n == 0) return EAT_OK;
+    if (!types || !times || !out) return fail(EAT_ERR_INVALID, "NULL argument");
+    DeviceGuard guard(net->device);
+    cudaError_t e = launch_next_departure(net->dev, types, times, n, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "next-departure kernel launch");
+    return EAT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// Host preprocessing: connections -> connection types -> clusters -> AP cover
+// (Section IV-A, graph representation and preprocessing algorithm).
+//
+// Layout produced (see eat_net_view in eat.h):
+//   row_ptr[V+1]  types grouped by tail stop u, each group ordered by (v, lambda)
+//   type_rec[4T]  {v, lambda, first departure, last departure}
+//   type_cl[T]    cl_base: cluster k of the type starts at cl[cl_base + k]
+//   cl[]          AP index of the start of each cluster of each type, plus one
+//                 end entry per type; only clusters between the type's first
+//                 and last departure are stored (the paper stores y per type)
+//   ap[2A]        {first term, (difference << 16) | terms}
+//
+// Stops are processed in parallel chunks (std::thread); each chunk builds with
+// local indices and a final pass shifts them to global positions.
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cstring>
+#include <thread>
+
+#include "eat_internal.h"
+
+namespace eat {
+
+namespace {
+
+struct Rec {
+    int32_t v, dur, dep;
+};
+
+inline bool rec_less(const Rec &a, const Rec &b) {
+    if (a.v != b.v) return a.v < b.v;
+    if (a.dur != b.dur) return a.dur < b.dur;
+    return a.dep < b.dep;
+}
+
+// Per-thread bitmaps for the greedy AP cover.
+struct Bits {
+    std::vector<uint64_t> present, covered;
+    void ensure(size_t nbits) {
+        size_t w = (nbits + 63) / 64;
+        if (present.size() < w) {
+            present.assign(w, 0);
+            covered.assign(w, 0);
+        }
+    }
+    bool get(const std::vector<uint64_t> &b, int32_t i) const { return (b[i >> 6] >> (i & 63)) & 1; }
+    static void set(std::vector<uint64_t> &b, int32_t i) { b[i >> 6] |= uint64_t(1) << (i & 63); }
+};
+
+thread_local Bits tl_bits;
+
+struct Chunk {
+    int32_t u_begin = 0, u_end = 0;
+    std::vector<int32_t> types_per_u;   // local row counts
+    std::vector<int32_t> type_rec, type_cl, cl;
+    std::vector<uint32_t> ap;
+    int64_t n_conn = 0;
+    int32_t n_edges = 0, max_clusters = 0;
+};
+
+void build_chunk(Chunk &ch, const std::vector<int64_t> &u_off, std::vector<Rec> &recs,
+                 int32_t width, int32_t t0) {
+    std::vector<int32_t> deps;
+    for (int32_t u = ch.u_begin; u < ch.u_end; ++u) {
+        Rec *b = recs.data() + u_off[u];
+        Rec *e = recs.data() + u_off[u + 1];
+        std::sort(b, e, rec_less);
+        int32_t n_types_u = 0;
+        int32_t last_v = -1;
+        for (Rec *p = b; p < e;) {
+            Rec *q = p;
+            deps.clear();
+            while (q < e && q->v == p->v && q->dur == p->dur) {
+                if (deps.empty() || deps.back() != q->dep) deps.push_back(q->dep);
+                ++q;
+            }
+            ch.n_conn += (int64_t)deps.size();
+            if (p->v != last_v) { ++ch.n_edges; last_v = p->v; }
+            const int32_t first = deps.front(), last = deps.back();
+            const int32_t k_first = (first - t0) / width, k_last = (last - t0) / width;
+            ch.max_clusters = std::max(ch.max_clusters, k_last - k_first + 1);
+            const int32_t cl_start = (int32_t)ch.cl.size();
+            ch.type_rec.insert(ch.type_rec.end(), {p->v, p->dur, first, last});
+            ch.type_cl.push_back(cl_start - k_first);
+            size_t i = 0;
+            for (int32_t k = k_first; k <= k_last; ++k) {
+                ch.cl.push_back((int32_t)(ch.ap.size() / 2));
+                size_t j = i;
+                const int64_t hi = (int64_t)t0 + (int64_t)(k + 1) * width;
+                while (j < deps.size() && deps[j] < hi) ++j;
+                if (j > i) ap_cover(deps.data() + i, (int32_t)(j - i), width, ch.ap);
+                i = j;
+            }
+            ch.cl.push_back((int32_t)(ch.ap.size() / 2));
+            ++n_types_u;
+            p = q;
+        }
+        ch.types_per_u.push_back(n_types_u);
+    }
+}
+
+}  // namespace
+
+// Greedy AP cover of one cluster (Section II, Arithmetic Progression Technique):
+// repeatedly take the smallest uncovered value a; among the APs a, a+d, a+2d, ...
+// that stay inside the set (one per later value, i.e. per difference d, each
+// extended as far as it goes) take the one covering the most uncovered values,
+// then the longest, then the smallest d.  Values are sorted and unique and span
+// less than `width_hint` seconds.  APs come out in increasing first term.
+void ap_cover(const int32_t *d, int32_t n, int32_t width_hint, std::vector<uint32_t> &out) {
+    if (n == 1) {
+        out.push_back((uint32_t)d[0]);
+        out.push_back(1u);
+        return;
+    }
+    const int32_t base = d[0];
+    const int32_t top = d[n - 1];
+    const int32_t span = top - base + 1;
+    (void)width_hint;
+    Bits &bits = tl_bits;
+    bits.ensure((size_t)span);
+    for (int32_t i = 0; i < n; ++i) Bits::set(bits.present, d[i] - base);
+    int32_t n_cov = 0, i = 0;
+    while (n_cov < n) {
+        while (bits.get(bits.covered, d[i] - base)) ++i;
+        const int32_t a = d[i];
+        int32_t best_unc = 1, best_len = 1, best_step = 0;
+        for (int32_t j = i + 1; j < n; ++j) {
+            const int32_t step = d[j] - a;
+            const int32_t max_len = (top - a) / step + 1;
+            if (max_len <= best_unc) break;  // no later (larger) step can win
+            int32_t len = 0, unc = 0;
+            for (int64_t t = a; t <= top && bits.get(bits.present, (int32_t)(t - base)); t += step) {
+                ++len;
+                unc += !bits.get(bits.covered, (int32_t)(t - base));
+            }
+            if (unc > best_unc || (unc == best_unc && len > best_len)) {
+                best_unc = unc;
+                best_len = len;
+                best_step = step;
+            }
+        }
+        for (int32_t m = 0; m < best_len; ++m) {
+            const int32_t off = a - base + m * best_step;
+            if (!bits.get(bits.covered, off)) {
+                Bits::set(bits.covered, off);
+                ++n_cov;
+            }
+        }
+        out.push_back((uint32_t)a);
+        out.push_back(((uint32_t)best_step << 16) | (uint32_t)best_len);
+    }
+    const size_t words = ((size_t)span + 63) / 64;
+    std::memset(bits.present.data(), 0, words * sizeof(uint64_t));
+    std::memset(bits.covered.data(), 0, words * sizeof(uint64_t));
+}
+
+int build_host(const eat_connections *c, int32_t width, int32_t t0, HostNet &h) {
+    const int32_t V = c->n_stops;
+    const int64_t C = c->n_conn;
+    if (V <= 0) return fail(EAT_ERR_INVALID, "n_stops must be >= 1");
+    if (C < 0 || C >= INT32_MAX) return fail(EAT_ERR_INVALID, "n_conn must be in [0, 2^31-1)");
+    if (C > 0 && (!c->u || !c->v || !c->dep || !c->dur))
+        return fail(EAT_ERR_INVALID, "connection arrays must not be NULL");
+    if (width < 1 || width > 65535) return fail(EAT_ERR_INVALID, "cluster_width must be in 1..65535");
+    for (int64_t i = 0; i < C; ++i) {
+        const int32_t u = c->u[i], v = c->v[i], dep = c->dep[i], dur = c->dur[i];
+        if (u < 0 || u >= V || v < 0 || v >= V)
+            return fail(EAT_ERR_INVALID, "connection " + std::to_string(i) + ": stop id out of range");
+        if (dur < 1)
+            return fail(EAT_ERR_INVALID, "connection " + std::to_string(i) + ": duration must be >= 1");
+        if (dep < t0)
+            return fail(EAT_ERR_INVALID, "connection " + std::to_string(i) + ": departure before t0");
+        if ((int64_t)dep - t0 >= (int64_t)INT32_MAX)
+            return fail(EAT_ERR_INVALID, "connection " + std::to_string(i) + ": departure too far after t0");
+        if ((int64_t)dep + dur >= (int64_t)INT32_MAX)
+            return fail(EAT_ERR_INVALID, "connection " + std::to_string(i) + ": arrival overflows int32");
+    }
+
+    // Counting sort of the connections by tail stop.
+    std::vector<int64_t> u_off((size_t)V + 1, 0);
+    for (int64_t i = 0; i < C; ++i) ++u_off[(size_t)c->u[i] + 1];
+    for (int32_t u = 0; u < V; ++u) u_off[u + 1] += u_off[u];
+    std::vector<Rec> recs((size_t)C);
+    {
+        std::vector<int64_t> pos(u_off.begin(), u_off.end() - 1);
+        for (int64_t i = 0; i < C; ++i) recs[pos[c->u[i]]++] = Rec{c->v[i], c->dur[i], c->dep[i]};
+    }
+
+    // Chunks of stops with about equal connection counts.
+    unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    const int n_chunks = (int)std::min<int64_t>((int64_t)hw * 4, V);
+    std::vector<Chunk> chunks((size_t)n_chunks);
+    {
+        int32_t u = 0;
+        for (int k = 0; k < n_chunks; ++k) {
+            const int64_t target = (C * (k + 1)) / n_chunks;
+            chunks[k].u_begin = u;
+            int32_t e = u;
+            if (k == n_chunks - 1) e = V;
+            else while (e < V && u_off[e] < target) ++e;
+            chunks[k].u_end = e;
+            u = e;
+        }
+    }
+    {
+        std::vector<std::thread> th;
+        std::atomic_int next{0};
+        auto work = [&]() {
+            for (;;) {
+                int k = next.fetch_add(1);
+                if (k >= n_chunks) return;
+                build_chunk(chunks[k], u_off, recs, width, t0);
+            }
+        };
+        for (unsigned t = 1; t < hw; ++t) th.emplace_back(work);
+        work();
+        for (auto &t : th) t.join();
+    }
+
+    // Concatenate chunks, shifting local indices to global ones.
+    int64_t T = 0, NCL = 0, NAP = 0;
+    std::vector<int64_t> t_off(n_chunks), cl_off(n_chunks), ap_off(n_chunks);
+    h = HostNet();
+    h.n_stops = V;
+    h.width = width;
+    h.t0 = t0;
+    for (int k = 0; k < n_chunks; ++k) {
+        t_off[k] = T;
+        cl_off[k] = NCL;
+        ap_off[k] = NAP;
+        T += (int64_t)chunks[k].type_cl.size();
+        NCL += (int64_t)chunks[k].cl.size();
+        NAP += (int64_t)chunks[k].ap.size() / 2;
+        h.n_conn += chunks[k].n_conn;
+        h.n_edges += chunks[k].n_edges;
+        h.max_clusters = std::max(h.max_clusters, chunks[k].max_clusters);
+    }
+    if (T >= INT32_MAX || NCL >= INT32_MAX || NAP >= INT32_MAX)
+        return fail(EAT_ERR_INVALID, "network too large for 32-bit indices");
+    h.n_types = (int32_t)T;
+    try {
+        h.row_ptr.resize((size_t)V + 1);
+        h.type_rec.resize((size_t)T * 4);
+        h.type_cl.resize((size_t)T);
+        h.cl.resize((size_t)NCL);
+        h.ap.resize((size_t)NAP * 2);
+    } catch (const std::bad_alloc &) {
+        return fail(EAT_ERR_OOM, "host allocation failed");
+    }
+    {
+        std::vector<std::thread> th;
+        auto copy = [&](int k) {
+            const Chunk &ch = chunks[k];
+            std::copy(ch.type_rec.begin(), ch.type_rec.end(), h.type_rec.begin() + t_off[k] * 4);
+            for (size_t i = 0; i < ch.type_cl.size(); ++i)
+                h.type_cl[t_off[k] + i] = ch.type_cl[i] + (int32_t)cl_off[k];
+            for (size_t i = 0; i < ch.cl.size(); ++i)
+                h.cl[cl_off[k] + i] = ch.cl[i] + (int32_t)ap_off[k];
+            std::copy(ch.ap.begin(), ch.ap.end(), h.ap.begin() + ap_off[k] * 2);
+        };
+        for (int k = 1; k < n_chunks; ++k) th.emplace_back(copy, k);
+        if (n_chunks > 0) copy(0);
+        for (auto &t : th) t.join();
+    }
+    int32_t r = 0;
+    for (int k = 0; k < n_chunks; ++k) {
+        const Chunk &ch = chunks[k];
+        for (int32_t i = 0; i < (int32_t)ch.types_per_u.size(); ++i) {
+            h.row_ptr[ch.u_begin + i] = r;
+            r += ch.types_per_u[i];
+            h.max_out_types = std::max(h.max_out_types, ch.types_per_u[i]);
+        }
+    }
+    h.row_ptr[V] = r;
+    return EAT_OK;
+}
+
+}  // namespace eat

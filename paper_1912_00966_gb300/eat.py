@@ -1,0 +1,286 @@
+"""Thin ctypes binding of libeat's C ABI (include/eat.h), with the same names.
+
+Only argument marshalling happens here: every step of a query runs in libeat's
+CUDA kernels.  Buffers may be torch tensors (CPU or CUDA) or numpy arrays; the
+binding passes their raw pointers and never copies or computes results itself.
+If libeat.so is missing this module raises ImportError: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libeat.so")
+
+EAT_INF = 2**31 - 1
+EAT_OK, EAT_ERR_INVALID, EAT_ERR_OOM, EAT_ERR_CUDA = 0, 1, 2, 3
+EAT_ERR_NO_CONVERGENCE, EAT_ERR_NO_DEVICE, EAT_ERR_WORKSPACE = 4, 5, 6
+EAT_MODE_AUTO, EAT_MODE_CTA, EAT_MODE_GRID = 0, 1, 2
+EAT_PLACE_AUTO, EAT_PLACE_SHARED, EAT_PLACE_GLOBAL_ARR, EAT_PLACE_GLOBAL = 0, 1, 2, 3
+EAT_MAX_NETS = 128
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libeat.so not found at {LIB_PATH}: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_vp = ctypes.c_void_p
+
+
+class eat_connections(ctypes.Structure):
+    _fields_ = [("n_stops", ctypes.c_int32), ("n_conn", ctypes.c_int64),
+                ("u", _vp), ("v", _vp), ("dep", _vp), ("dur", _vp)]
+
+
+class eat_build_opts(ctypes.Structure):
+    _fields_ = [("cluster_width", ctypes.c_int32), ("t0", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class eat_stats(ctypes.Structure):
+    _fields_ = [("n_stops", ctypes.c_int32), ("n_types", ctypes.c_int32),
+                ("n_edges", ctypes.c_int32), ("cluster_width", ctypes.c_int32),
+                ("t0", ctypes.c_int32), ("max_clusters", ctypes.c_int32),
+                ("max_out_types", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("n_conn", ctypes.c_int64), ("n_ap", ctypes.c_int64),
+                ("n_cl", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class eat_net_view(ctypes.Structure):
+    _fields_ = [("row_ptr", _vp), ("type_rec", _vp), ("type_cl", _vp), ("cl", _vp),
+                ("ap", _vp)]
+
+
+class eat_counters(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("vertices", ctypes.c_int64),
+                ("types", ctypes.c_int64), ("evals", ctypes.c_int64),
+                ("lookups", ctypes.c_int64), ("aps", ctypes.c_int64),
+                ("relaxed", ctypes.c_int64)]
+
+
+COUNTER_FIELDS = ("rounds", "vertices", "types", "evals", "lookups", "aps", "relaxed")
+
+
+class eat_query_opts(ctypes.Structure):
+    _fields_ = [("max_rounds", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("vwarp", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("placement", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("status", _vp), ("counters", _vp)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("eat_last_error", ctypes.c_char_p, [])
+_sig("eat_version", ctypes.c_int32, [])
+_sig("eat_build", ctypes.c_int, [ctypes.POINTER(eat_connections), ctypes.POINTER(eat_build_opts),
+                                 ctypes.POINTER(_vp)])
+_sig("eat_free", None, [_vp])
+_sig("eat_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(eat_stats)])
+_sig("eat_net_host_view", ctypes.c_int, [_vp, ctypes.POINTER(eat_net_view)])
+_sig("eat_query", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp])
+_sig("eat_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(_vp), ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.POINTER(eat_query_opts)])
+_sig("eat_query_batch", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t,
+                                       ctypes.POINTER(eat_query_opts), _vp])
+_sig("eat_query_batch_multi", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, _vp, _vp, _vp,
+                                             ctypes.c_int32, _vp, _vp, _vp, ctypes.c_size_t,
+                                             ctypes.POINTER(eat_query_opts), _vp])
+_sig("eat_next_departure", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, _vp])
+
+EXPORTED = ("eat_last_error", "eat_version", "eat_build", "eat_free", "eat_get_stats",
+            "eat_net_host_view", "eat_query", "eat_workspace_bytes", "eat_query_batch",
+            "eat_query_batch_multi", "eat_next_departure")
+
+
+class EatError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.eat_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {code}: {msg}")
+
+
+def _check(rc, where):
+    if rc != EAT_OK:
+        raise EatError(rc, where)
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffers must be contiguous")
+        return x.ctypes.data
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Net:
+    """Owning handle of an eat_net (released by eat_free on close or garbage collection)."""
+
+    def __init__(self, handle, keep=None):
+        self._h = _vp(handle)
+        self._keep = keep
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("network already freed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.eat_free(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stats(self):
+        return eat_get_stats(self)
+
+
+def eat_build(n_stops, u, v, dep, dur, cluster_width=0, t0=0, device=0) -> Net:
+    """Preprocess connections (host int32 arrays) into a device-resident network."""
+    u, v, dep, dur = _i32(u), _i32(v), _i32(dep), _i32(dur)
+    n = u.shape[0]
+    if not (v.shape[0] == dep.shape[0] == dur.shape[0] == n):
+        raise ValueError("connection arrays differ in length")
+    c = eat_connections(int(n_stops), int(n), u.ctypes.data, v.ctypes.data, dep.ctypes.data,
+                        dur.ctypes.data)
+    o = eat_build_opts(int(cluster_width), int(t0), int(device), 0)
+    h = _vp()
+    _check(_lib.eat_build(ctypes.byref(c), ctypes.byref(o), ctypes.byref(h)), "eat_build")
+    return Net(h.value)
+
+
+def eat_free(net: Net) -> None:
+    net.close()
+
+
+def eat_get_stats(net: Net) -> dict:
+    s = eat_stats()
+    _check(_lib.eat_get_stats(net.handle, ctypes.byref(s)), "eat_get_stats")
+    return {f: getattr(s, f) for f, _ in eat_stats._fields_}
+
+
+def eat_net_host_view(net: Net) -> dict:
+    """Copies of the built arrays: row_ptr, type_rec [T, 4], type_cl, cl, ap [A, 2]."""
+    st = eat_get_stats(net)
+    view = eat_net_view()
+    _check(_lib.eat_net_host_view(net.handle, ctypes.byref(view)), "eat_net_host_view")
+
+    def arr(ptr, n, dt):
+        if n == 0:
+            return np.zeros(0, dtype=dt)
+        buf = (ctypes.c_char * (n * np.dtype(dt).itemsize)).from_address(ptr)
+        return np.frombuffer(buf, dtype=dt).copy()
+
+    T, V = st["n_types"], st["n_stops"]
+    return {
+        "row_ptr": arr(view.row_ptr, V + 1, np.int32),
+        "type_rec": arr(view.type_rec, 4 * T, np.int32).reshape(T, 4),
+        "type_cl": arr(view.type_cl, T, np.int32),
+        "cl": arr(view.cl, st["n_cl"], np.int32),
+        "ap": arr(view.ap, 2 * st["n_ap"], np.uint32).reshape(-1, 2),
+    }
+
+
+def _opts(max_rounds=0, block=0, vwarp=0, mode=0, placement=0, status=None, counters=None):
+    return eat_query_opts(int(max_rounds), int(block), int(vwarp), int(mode), int(placement), 0,
+                          _ptr(status), _ptr(counters))
+
+
+def eat_query(net: Net, s: int, t_s: int, out=None, counters: bool = False):
+    """One blocking query; `out` may be a host/device buffer of n_stops int32 (allocated as
+    numpy when None).  Returns out, or (out, counters dict) if counters=True."""
+    if out is None:
+        out = np.empty(eat_get_stats(net)["n_stops"], dtype=np.int32)
+    c = eat_counters()
+    _check(_lib.eat_query(net.handle, int(s), int(t_s), _ptr(out), ctypes.byref(c)), "eat_query")
+    if counters:
+        return out, {f: getattr(c, f) for f in COUNTER_FIELDS}
+    return out
+
+
+def eat_workspace_bytes(nets, n, **opts) -> int:
+    if isinstance(nets, Net):
+        nets = [nets]
+    arr = (_vp * len(nets))(*[x.handle.value for x in nets])
+    o = _opts(**opts)
+    return int(_lib.eat_workspace_bytes(arr, len(nets), int(n), ctypes.byref(o)))
+
+
+def eat_query_batch(net: Net, sources, times, out, workspace=None, workspace_bytes=None,
+                    stream=None, **opts):
+    """n queries on one network.  sources/times/out: torch tensors or numpy arrays, host or
+    device; out holds n * n_stops int32.  Asynchronous when every buffer is on the device."""
+    n = int(sources.shape[0])
+    o = _opts(**opts)
+    wb = workspace_bytes if workspace_bytes is not None else (
+        workspace.numel() * workspace.element_size() if workspace is not None else 0)
+    _check(_lib.eat_query_batch(net.handle, _ptr(sources), _ptr(times), n, _ptr(out),
+                                _ptr(workspace), int(wb), ctypes.byref(o),
+                                _stream_handle(stream)), "eat_query_batch")
+    return out
+
+
+def eat_query_batch_multi(nets, net_idx, sources, times, out, arr_offsets, workspace=None,
+                          workspace_bytes=None, stream=None, **opts):
+    """n queries over several networks in one launch (see eat.h)."""
+    arr = (_vp * len(nets))(*[x.handle.value for x in nets])
+    n = int(sources.shape[0])
+    o = _opts(**opts)
+    wb = workspace_bytes if workspace_bytes is not None else (
+        workspace.numel() * workspace.element_size() if workspace is not None else 0)
+    _check(_lib.eat_query_batch_multi(arr, len(nets), _ptr(net_idx), _ptr(sources), _ptr(times),
+                                      n, _ptr(out), _ptr(arr_offsets), _ptr(workspace), int(wb),
+                                      ctypes.byref(o), _stream_handle(stream)),
+           "eat_query_batch_multi")
+    return out
+
+
+def eat_next_departure(net: Net, types, times, out, stream=None):
+    """out[i] = least departure >= times[i] of type types[i] (device int32 buffers)."""
+    _check(_lib.eat_next_departure(net.handle, _ptr(types), _ptr(times), int(types.shape[0]),
+                                   _ptr(out), _stream_handle(stream)), "eat_next_departure")
+    return out
+
+
+def eat_version() -> int:
+    return int(_lib.eat_version())
+
+
+def eat_last_error() -> str:
+    return _lib.eat_last_error().decode(errors="replace")

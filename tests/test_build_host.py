@@ -1,0 +1,143 @@
+"""libeat's host preprocessing (Section IV-A layout) against the oracle's definitions (no GPU).
+
+A host-only build (device = -1) exposes the built arrays; they must encode exactly
+the oracle's connection types (Section III-B), cluster split (Section III-D) and
+greedy AP cover (Section II), and the builder must reject invalid input.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.ap_greedy import ap_cover, ap_expand
+from paper_1912_00966_gb300 import eat
+
+INF = 2**31 - 1
+
+
+def _build(tt, **kw):
+    return eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=-1, **kw)
+
+
+def _decode(net):
+    """Per type (u, v, lambda) -> {cluster k: [(first, last, diff), ...]} from the host view."""
+    hv = eat.eat_net_host_view(net)
+    st = eat.eat_get_stats(net)
+    out = {}
+    rp, rec, clb, cl, ap = hv["row_ptr"], hv["type_rec"], hv["type_cl"], hv["cl"], hv["ap"]
+    for u in range(st["n_stops"]):
+        for t in range(rp[u], rp[u + 1]):
+            v, lam, first, last = (int(x) for x in rec[t])
+            W, t0 = st["cluster_width"], st["t0"]
+            clusters = {}
+            for k in range((first - t0) // W, (last - t0) // W + 1):
+                lo, hi = int(cl[clb[t] + k]), int(cl[clb[t] + k + 1])
+                aps = []
+                for a in range(lo, hi):
+                    start, packed = int(ap[a, 0]), int(ap[a, 1])
+                    step, cnt = packed >> 16, packed & 0xFFFF
+                    aps.append((start, start + (cnt - 1) * step, step))
+                if aps:
+                    clusters[k] = aps
+            out[(u, v, lam)] = (first, last, clusters)
+    return out, hv, st
+
+
+@pytest.mark.parametrize("make,width,t0", [
+    (synth.small_grid, 0, 0),
+    (synth.small_grid, 900, 0),
+    (synth.small_grid, 600, 17000),
+    (lambda: synth.tiny_random(9, 400, 3, t_max=20000, dur_max=300), 3600, 0),
+    (lambda: synth.tiny_random(5, 300, 4, t_max=500, dur_max=5), 7, 0),
+])
+def test_layout_matches_oracle(make, width, t0):
+    tt = make()
+    net = _build(tt, cluster_width=width, t0=t0)
+    got, hv, st = _decode(net)
+    W = width or 3600
+    types = oracle.connection_types(tt)
+    assert set(got) == set(types)
+    assert st["n_types"] == len(types)
+    assert st["n_conn"] == sum(len(d) for d in types.values())
+    # types ordered by (u, v, lambda) inside each row
+    keys = [(int(u), int(r[0]), int(r[1])) for u in range(st["n_stops"])
+            for r in hv["type_rec"][hv["row_ptr"][u]:hv["row_ptr"][u + 1]]]
+    assert keys == sorted(keys)
+    for key, deps in types.items():
+        first, last, clusters = got[key]
+        assert first == deps[0] and last == deps[-1]
+        want = oracle.cluster_sets(deps, width=W, t0=t0)
+        assert set(clusters) == set(want)
+        for k, vals in want.items():
+            assert ap_expand(clusters[k]) == vals          # exact cover, no extra departures
+            assert clusters[k] == ap_cover(vals)           # same greedy decisions
+            starts = [a[0] for a in clusters[k]]
+            assert starts == sorted(starts)
+
+
+def test_duplicates_merged_and_stats():
+    tt = synth.small_grid()
+    twice = synth.Timetable("dup", tt.n_stops, np.concatenate([tt.u, tt.u]),
+                            np.concatenate([tt.v, tt.v]), np.concatenate([tt.dep, tt.dep]),
+                            np.concatenate([tt.dur, tt.dur]), np.concatenate([tt.trip, tt.trip]),
+                            np.concatenate([tt.seq, tt.seq]))
+    a = eat.eat_get_stats(_build(tt))
+    b = eat.eat_get_stats(_build(twice))
+    for k in ("n_types", "n_conn", "n_ap", "n_cl", "n_edges"):
+        assert a[k] == b[k]
+    assert a["n_conn"] == tt.n_conn
+
+
+def test_paper_worked_example_through_builder():
+    # Section III-C: departures 8:00, 8:15, ..., 18:00 on one type are a single AP
+    # (8:00, 18:00, 15 min) when no cluster boundary cuts them.
+    deps = np.arange(28800, 64801, 900, dtype=np.int32)
+    n = deps.shape[0]
+    z = np.zeros(n, np.int32)
+    tt = synth.Timetable("ex", 2, z, z + 1, deps, z + 60, z, z)
+    got, _, st = _decode(_build(tt, cluster_width=65535, t0=0))
+    assert got[(0, 1, 60)][2] == {0: [(28800, 64800, 900)]}
+    # With hourly clusters the same departures split into one AP per hour.
+    got, _, _ = _decode(_build(tt))
+    assert got[(0, 1, 60)][2][8] == [(28800, 31500, 900)]
+    assert got[(0, 1, 60)][2][18] == [(64800, 64800, 0)]
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("u", 10, "stop id"), ("v", -1, "stop id"), ("dur", 0, "duration"),
+    ("dep", -5, "before t0"), ("dep", INF - 10, "overflow"),
+])
+def test_invalid_connections_rejected(field, value, msg):
+    tt = synth.tiny_random(10, 50, 1)
+    arrs = {f: getattr(tt, f).copy() for f in ("u", "v", "dep", "dur")}
+    arrs[field][7] = value
+    if field == "dep" and value > 0:
+        arrs["dur"][7] = 20
+    with pytest.raises(eat.EatError) as ei:
+        eat.eat_build(10, arrs["u"], arrs["v"], arrs["dep"], arrs["dur"], device=-1)
+    assert ei.value.code == eat.EAT_ERR_INVALID
+    assert msg in str(ei.value)
+
+
+def test_invalid_options_rejected():
+    tt = synth.tiny_random(10, 50, 1)
+    for kw in ({"cluster_width": 65536}, {"cluster_width": -3}):
+        with pytest.raises(eat.EatError) as ei:
+            _build(tt, **kw)
+        assert ei.value.code == eat.EAT_ERR_INVALID
+    with pytest.raises(eat.EatError) as ei:
+        eat.eat_build(0, [], [], [], [], device=-1)
+    assert ei.value.code == eat.EAT_ERR_INVALID
+    with pytest.raises(eat.EatError) as ei:
+        _build(tt, t0=10**6)
+    assert ei.value.code == eat.EAT_ERR_INVALID
+
+
+def test_empty_timetable_and_host_only_queries():
+    net = eat.eat_build(4, [], [], [], [], device=-1)
+    st = eat.eat_get_stats(net)
+    assert st["n_types"] == 0 and st["n_ap"] == 0
+    assert eat.eat_net_host_view(net)["row_ptr"].tolist() == [0, 0, 0, 0, 0]
+    with pytest.raises(eat.EatError) as ei:
+        eat.eat_query(net, 0, 0)
+    assert ei.value.code == eat.EAT_ERR_NO_DEVICE

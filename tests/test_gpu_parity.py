@@ -1,0 +1,289 @@
+"""GPU parity: libeat's CUDA path (through the C ABI) against the oracle, bit-exact.
+
+Arrival times are int32, so every comparison is exact equality with the
+connection-scan oracle (Algorithm 1) on the same seeded inputs; large cases are
+compared on sampled queries and checked by the oracle's exactness certificate.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+INF = 2**31 - 1
+
+
+@pytest.fixture(scope="module")
+def eat():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_00966_gb300 import eat as mod
+    return mod
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+class Case:
+    def __init__(self, eat, tt, **kw):
+        self.tt = tt
+        self.net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=0, **kw)
+        self.sc = oracle.SortedConnections(tt)
+        self.V = tt.n_stops
+
+    def oracle_rows(self, src, ts):
+        out, _ = oracle.csa_many(self.sc, src, ts, 8)
+        return out
+
+    def run(self, eat, src, ts, **opts):
+        n = len(src)
+        out = torch.empty(n * self.V, dtype=torch.int32, device="cuda")
+        status = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros((n, 7), dtype=torch.int64, device="cuda")
+        eat.eat_query_batch(self.net, _dev(src), _dev(ts), out, status=status, counters=cnt, **opts)
+        torch.cuda.synchronize()
+        return out.view(n, self.V).cpu().numpy(), status.cpu().numpy(), cnt.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def small(eat):
+    return Case(eat, synth.small_grid())
+
+
+@pytest.fixture(scope="module")
+def city(eat):
+    return Case(eat, synth.city())
+
+
+def test_smoke_entry(eat):
+    import __graft_entry__
+    __graft_entry__.smoke()
+
+
+def test_single_query_edge_cases(eat, small):
+    tt = small.tt
+    unserved = int(np.setdiff1d(np.arange(tt.n_stops), np.concatenate([tt.u, tt.v]))[0])
+    exact_dep = int(tt.dep[tt.u == 0].min())
+    cases = [(0, 28800), (0, 0), (0, 200000), (unserved, 30000), (0, exact_dep),
+             (0, exact_dep + 1), (0, -1000), (0, INF), (tt.n_stops - 1, 40000)]
+    for s, t_s in cases:
+        got = eat.eat_query(small.net, s, t_s)
+        want = oracle.csa(small.sc, s, t_s)
+        assert np.array_equal(got, want), (s, t_s)
+        # device output buffer
+        out = torch.empty(tt.n_stops, dtype=torch.int32, device="cuda")
+        eat.eat_query(small.net, s, t_s, out)
+        assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_batch_small_random(eat, small):
+    q = synth.random_queries(small.tt, 300, 21)
+    got, status, cnt = small.run(eat, q.source, q.t_s)
+    assert (status == 0).all()
+    assert np.array_equal(got, small.oracle_rows(q.source, q.t_s))
+    rounds, vert, types, evals, lookups, aps, relaxed = cnt.T
+    assert (rounds >= 1).all() and (rounds <= small.V + 1).all()
+    assert (types >= evals).all() and (evals >= lookups).all()
+    reach = (got < INF).sum(axis=1)
+    assert (relaxed >= reach - 1).all()
+    assert (vert >= reach).all()
+
+
+def test_host_buffers_match_device(eat, small):
+    q = synth.random_queries(small.tt, 40, 5)
+    host = np.empty((40, small.V), dtype=np.int32)
+    eat.eat_query_batch(small.net, q.source, q.t_s, host)
+    pinned = torch.empty((40, small.V), dtype=torch.int32).pin_memory()
+    eat.eat_query_batch(small.net, torch.as_tensor(q.source), torch.as_tensor(q.t_s), pinned)
+    want = small.oracle_rows(q.source, q.t_s)
+    assert np.array_equal(host, want)
+    assert np.array_equal(pinned.numpy(), want)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_tiny_random_nets_all_sources(eat, seed):
+    tt = synth.tiny_random(2 + seed % 13, 1 + (seed * 37) % 300, 500 + seed, t_max=300 + 50 * seed,
+                           dur_max=1 + seed % 60)
+    case = Case(eat, tt, cluster_width=[3600, 60, 7, 1][seed % 4])
+    src = np.repeat(np.arange(tt.n_stops), 4).astype(np.int32)
+    rng = np.random.default_rng(seed)
+    ts = rng.integers(-5, int(tt.dep.max()) + 10, size=src.shape[0]).astype(np.int32)
+    got, status, _ = case.run(eat, src, ts)
+    assert (status == 0).all()
+    want = case.oracle_rows(src, ts)
+    assert np.array_equal(got, want)
+    for i in range(0, len(src), 7):
+        assert np.array_equal(got[i], oracle.brute.foremost_dijkstra(
+            tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, int(src[i]), int(ts[i])))
+
+
+@pytest.mark.parametrize("vwarp", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("block", [64, 256, 1024])
+def test_mapping_variants(eat, city, vwarp, block):
+    q = synth.random_queries(city.tt, 48, 100 + vwarp)
+    got, status, _ = city.run(eat, q.source, q.t_s, vwarp=vwarp, block=block)
+    assert (status == 0).all()
+    assert np.array_equal(got, city.oracle_rows(q.source, q.t_s))
+
+
+@pytest.mark.parametrize("placement", [1, 2, 3])
+def test_memory_placements(eat, small, city, placement):
+    for case in (small, city):
+        q = synth.random_queries(case.tt, 64, 7 + placement)
+        got, status, _ = case.run(eat, q.source, q.t_s, placement=placement)
+        assert (status == 0).all()
+        assert np.array_equal(got, case.oracle_rows(q.source, q.t_s))
+
+
+def test_city_256_queries_default_launch(eat, city):
+    """The benchmark's workload and launch configuration (256 queries, default options)."""
+    q = synth.random_queries(city.tt, 256, 0xC17)
+    got, status, cnt = city.run(eat, q.source, q.t_s)
+    assert (status == 0).all()
+    assert np.array_equal(got, city.oracle_rows(q.source, q.t_s))
+    for i in range(0, 256, 64):
+        assert oracle.certify(city.tt, int(q.source[i]), int(q.t_s[i]), got[i]) == (0, -1)
+
+
+def test_repeatable(eat, city):
+    q = synth.random_queries(city.tt, 128, 3)
+    first, _, _ = city.run(eat, q.source, q.t_s)
+    for _ in range(4):
+        again, _, _ = city.run(eat, q.source, q.t_s)
+        assert np.array_equal(first, again)
+
+
+def test_monotone_in_departure_time(eat, city):
+    s = int(synth.random_queries(city.tt, 1, 77).source[0])
+    ts = np.arange(18000, 80000, 1800, dtype=np.int32)
+    got, _, _ = city.run(eat, np.full(ts.shape, s, np.int32), ts)
+    g = got.astype(np.int64)
+    g[:, s] = 0
+    assert (np.diff(g, axis=0) >= 0).all()
+
+
+def test_round_cap_reports_no_convergence(eat, small):
+    q = synth.random_queries(small.tt, 64, 8)
+    full, _, cnt = small.run(eat, q.source, q.t_s)
+    capped, status, _ = small.run(eat, q.source, q.t_s, max_rounds=1)
+    needs_more = cnt[:, 0] > 1
+    assert needs_more.any()
+    assert (status[needs_more] == eat.EAT_ERR_NO_CONVERGENCE).all()
+    assert (status[~needs_more] == 0).all()
+    assert (capped.astype(np.int64) >= full).all()          # upper bounds only
+
+
+def test_invalid_source_and_workspace(eat, small):
+    src = np.array([0, small.V, -3, 5], np.int32)
+    ts = np.full(4, 30000, np.int32)
+    got, status, _ = small.run(eat, src, ts)
+    assert status.tolist()[1:3] == [eat.EAT_ERR_INVALID] * 2
+    assert (got[1] == INF).all() and (got[2] == INF).all()
+    assert np.array_equal(got[[0, 3]], small.oracle_rows(src[[0, 3]], ts[[0, 3]]))
+    with pytest.raises(eat.EatError) as ei:
+        eat.eat_query(small.net, small.V, 0)
+    assert ei.value.code == eat.EAT_ERR_INVALID
+    need = eat.eat_workspace_bytes(small.net, 4)
+    ws = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    out = torch.empty(4 * small.V, dtype=torch.int32, device="cuda")
+    with pytest.raises(eat.EatError) as ei:
+        eat.eat_query_batch(small.net, _dev(src), _dev(ts), out, workspace=ws)
+    assert ei.value.code == eat.EAT_ERR_WORKSPACE
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    eat.eat_query_batch(small.net, _dev(src[[0, 3]]), _dev(ts[[0, 3]]), out, workspace=ws)
+    torch.cuda.synchronize()
+
+
+def test_empty_network_and_empty_batch(eat):
+    net = eat.eat_build(5, [], [], [], [], device=0)
+    got = eat.eat_query(net, 2, 100)
+    assert got.tolist() == [INF, INF, 100, INF, INF]
+    out = torch.empty(0, dtype=torch.int32, device="cuda")
+    eat.eat_query_batch(net, _dev([]), _dev([]), out)
+
+
+def test_ragged_multi_network_batch(eat, small):
+    nets = [small] + [Case(eat, synth.grid_timetable(n, int(np.ceil(50 * n / 1024)), 900 + n,
+                                                       force_stop0=False)) for n in (1500, 3100, 7000)]
+    Q = 200
+    qs = synth.random_queries([c.tt for c in nets], Q, 42)
+    sizes = np.array([nets[i].V for i in qs.net], np.int64)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    out = torch.full((int(sizes.sum()),), -7, dtype=torch.int32, device="cuda")
+    status = torch.full((Q,), -1, dtype=torch.int32, device="cuda")
+    eat.eat_query_batch_multi([c.net for c in nets], _dev(qs.net), _dev(qs.source), _dev(qs.t_s),
+                              out, torch.as_tensor(offs).cuda(), status=status)
+    torch.cuda.synchronize()
+    flat = out.cpu().numpy()
+    assert (status.cpu().numpy() == 0).all()
+    for i in range(Q):
+        c = nets[qs.net[i]]
+        want = oracle.csa(c.sc, int(qs.source[i]), int(qs.t_s[i]))
+        assert np.array_equal(flat[offs[i]:offs[i] + c.V], want), i
+    # Host query arrays take the staged path and give the same rows.
+    out2 = torch.full_like(out, -7)
+    eat.eat_query_batch_multi([c.net for c in nets], qs.net, qs.source, qs.t_s, out2, offs)
+    assert torch.equal(out, out2)
+
+
+def _type_departures(case, eat):
+    hv = eat.eat_net_host_view(case.net)
+    types = oracle.connection_types(case.tt)
+    keys = []
+    for u in range(case.V):
+        for t in range(hv["row_ptr"][u], hv["row_ptr"][u + 1]):
+            v, lam = int(hv["type_rec"][t][0]), int(hv["type_rec"][t][1])
+            keys.append(types[(u, v, lam)])
+    return keys
+
+
+@pytest.mark.parametrize("which", ["small", "city"])
+def test_next_departure_lookup(eat, small, city, which):
+    case = small if which == "small" else city
+    deps = _type_departures(case, eat)
+    rng = np.random.default_rng(3)
+    pick = range(len(deps)) if which == "small" else rng.choice(len(deps), 1500, replace=False)
+    T, E = [], []
+    for t in pick:
+        d = deps[t]
+        probes = {d[0] - 1, d[0], d[0] + 1, d[-1] - 1, d[-1], d[-1] + 1, -5, INF - 1}
+        for x in d[:: max(1, len(d) // 12)]:
+            probes.update({x - 1, x, x + 1, x // 3600 * 3600, x // 3600 * 3600 - 1})
+        probes.update(int(y) for y in rng.integers(d[0] - 100, d[-1] + 100, size=6))
+        for e in probes:
+            T.append(int(t))
+            E.append(int(e))
+    out = torch.empty(len(T), dtype=torch.int32, device="cuda")
+    eat.eat_next_departure(case.net, _dev(T), _dev(E), out)
+    got = out.cpu().numpy()
+    want = np.array([oracle.next_departure(deps[t], e) for t, e in zip(T, E)], np.int64)
+    assert np.array_equal(got.astype(np.int64), want)
+
+
+@pytest.mark.parametrize("width", [60, 900, 7200, 65535])
+def test_cluster_widths(eat, width):
+    tt = synth.small_grid(seed_offset=5)
+    case = Case(eat, tt, cluster_width=width, t0=min(width // 3, 17000))
+    q = synth.random_queries(tt, 96, width)
+    got, status, _ = case.run(eat, q.source, q.t_s)
+    assert (status == 0).all()
+    assert np.array_equal(got, case.oracle_rows(q.source, q.t_s))
+
+
+def test_large_network_sampled(eat):
+    """200,000-stop network, about 46 M connections, 1,024 queries in one launch; sampled rows
+    are compared with the oracle exactly and more rows are certified."""
+    tt = synth.large()
+    case = Case(eat, tt)
+    q = synth.random_queries(tt, 1024, 0x1A)
+    got, status, cnt = case.run(eat, q.source, q.t_s)
+    assert (status == 0).all()
+    idx = np.random.default_rng(0).choice(1024, 12, replace=False)
+    want = case.oracle_rows(q.source[idx], q.t_s[idx])
+    assert np.array_equal(got[idx], want)
+    for i in np.random.default_rng(1).choice(1024, 4, replace=False):
+        assert oracle.certify(tt, int(q.source[i]), int(q.t_s[i]), got[i]) == (0, -1)
