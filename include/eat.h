@@ -259,6 +259,45 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
 int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *times,
                        int32_t n, int32_t *out, void *stream);
 
+/*
+ * eat_query_batch_noalloc -- eat_query_batch for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this entry point exists for
+ * users of the library, not for the method.
+ *
+ * Who needs it: code that is not allowed to call cudaMalloc and therefore
+ * cannot provide the workspace eat_query_batch asks for -- for example a
+ * plugin whose host application owns all device memory through its own
+ * allocator or budget, or a serving loop that admits work against a fixed
+ * memory reservation and must not grow it per call.  Such a caller still
+ * passes its own input and output buffers; the frontier queues that
+ * eat_query_batch keeps in the workspace live instead in one fixed scratch
+ * array inside libeat (EAT_NOALLOC_SCRATCH_BYTES = 16 MiB), which every GPU
+ * that loads the library holds until the process exits.
+ *
+ * Behaviour:
+ *   - Same queries and results as eat_query_batch (same kernel); sources,
+ *     times and arr_out must be device memory of the network's device.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (once per device, with that device current); make that first call before
+ *     any stream capture on the device.
+ *   - All calls share the one scratch array and it keeps the previous call's
+ *     contents; the call clears what must start at zero.  Calls whose GPU work
+ *     overlaps (on different streams or threads, for any network on the same
+ *     device) race on the scratch and give wrong results: serialise them.
+ *   - Limit: each concurrently running query needs 8 * n_stops bytes of the
+ *     scratch (rounded up), so the network may have at most 2,000,000 stops;
+ *     fewer queries then run at once and the rest wait in the same launch.
+ *     Larger networks are rejected with EAT_ERR_INVALID.
+ * Errors: EAT_ERR_INVALID (host buffers, network too large, bad options),
+ * EAT_ERR_NO_DEVICE, EAT_ERR_CUDA.
+ */
+#define EAT_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define EAT_NOALLOC_MAX_STOPS 2000000
+int eat_query_batch_noalloc(const eat_net *net, const int32_t *sources, const int32_t *times,
+                            int32_t n, int32_t *arr_out, const eat_query_opts *opts,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -551,3 +551,87 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ no-allocation entry point
+
+// Fixed scratch for eat_query_batch_noalloc: the work counter (first 256 bytes)
+// and the per-block frontier queues.  In host code this name is only a stand-in
+// for the device array; its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[EAT_NOALLOC_SCRATCH_BYTES];
+
+namespace eat {
+
+static std::mutex g_noalloc_lock;
+static void *g_noalloc_ptr[64];
+
+// Looks up the scratch array's device address once per device (the device is
+// current when this runs).
+static int noalloc_scratch(int dev, void **out) {
+    std::lock_guard<std::mutex> g(g_noalloc_lock);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return EAT_OK;
+}
+
+}  // namespace eat
+
+extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *sources,
+                                       const int32_t *times, int32_t n, int32_t *arr_out,
+                                       const eat_query_opts *opts, void *stream) {
+    clear_error();
+    if (!net) return fail(EAT_ERR_INVALID, "NULL network");
+    if (net->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
+    if (net->device >= 64) return fail(EAT_ERR_INVALID, "device ordinal out of range");
+    if (n < 0) return fail(EAT_ERR_INVALID, "n must be >= 0");
+    if (net->host.n_stops > EAT_NOALLOC_MAX_STOPS)
+        return fail(EAT_ERR_INVALID, "network has " + std::to_string(net->host.n_stops) +
+                                         " stops; the no-allocation scratch (16 MiB) serves at most " +
+                                         std::to_string(EAT_NOALLOC_MAX_STOPS));
+    if (n == 0) return EAT_OK;
+    if (!sources || !times || !arr_out) return fail(EAT_ERR_INVALID, "NULL query array");
+    DeviceGuard guard(net->device);
+    if (!is_device_ptr(sources) || !is_device_ptr(times) || !is_device_ptr(arr_out))
+        return fail(EAT_ERR_INVALID, "sources, times and arr_out must be device memory");
+    Plan p;
+    int rc = make_plan(net->device, net->host.n_stops, n, 1, opts, p);
+    if (rc) return rc;
+    // Fewer persistent blocks so that their queues fit the fixed scratch.
+    const size_t per_block = (size_t)p.queue_stride * 4 + (size_t)p.mask_stride * 4;
+    const size_t fit = (EAT_NOALLOC_SCRATCH_BYTES - kWsHeader) / per_block;
+    if (fit < 1)
+        return fail(EAT_ERR_INVALID, "network too large for the no-allocation scratch");
+    const int grid = (int)std::min<size_t>((size_t)p.grid, fit);
+    void *scratch = nullptr;
+    rc = noalloc_scratch(net->device, &scratch);
+    if (rc) return rc;
+    char *w = (char *)scratch;
+    QueryArgs qa;
+    qa.net_idx = nullptr;
+    qa.src = sources;
+    qa.ts = times;
+    qa.arr_off = nullptr;
+    qa.arr_out = arr_out;
+    qa.queues = (int32_t *)(w + kWsHeader);
+    qa.gmask = (uint32_t *)(w + kWsHeader + (size_t)grid * (size_t)p.queue_stride * 4);
+    qa.work = (int32_t *)w;
+    qa.status = opts ? opts->status : nullptr;
+    qa.counters = opts ? opts->counters : nullptr;
+    qa.queue_stride = p.queue_stride;
+    qa.mask_stride = p.mask_stride;
+    qa.n = n;
+    qa.n_nets = 1;
+    qa.max_rounds = (opts && opts->max_rounds > 0) ? opts->max_rounds : net->host.n_stops + 1;
+    qa.vw_log2 = p.vw_log2;
+    cudaStream_t st = (cudaStream_t)stream;
+    // The query counter must start at zero; the queues need no clearing.
+    cudaError_t e = cudaMemsetAsync(qa.work, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-allocation scratch)");
+    e = launch_cta(&net->dev, 1, qa, p.mem, grid, p.block, p.smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "CTA kernel launch");
+    return EAT_OK;
+}

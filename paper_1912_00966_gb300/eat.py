@@ -95,10 +95,12 @@ _sig("eat_query_batch_multi", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32
                                              ctypes.c_int32, _vp, _vp, _vp, ctypes.c_size_t,
                                              ctypes.POINTER(eat_query_opts), _vp])
 _sig("eat_next_departure", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, _vp])
+_sig("eat_query_batch_noalloc", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp,
+                                               ctypes.POINTER(eat_query_opts), _vp])
 
 EXPORTED = ("eat_last_error", "eat_version", "eat_build", "eat_free", "eat_get_stats",
             "eat_net_host_view", "eat_query", "eat_workspace_bytes", "eat_query_batch",
-            "eat_query_batch_multi", "eat_next_departure")
+            "eat_query_batch_multi", "eat_next_departure", "eat_query_batch_noalloc")
 
 
 class EatError(RuntimeError):
@@ -268,6 +270,17 @@ def eat_query_batch_multi(nets, net_idx, sources, times, out, arr_offsets, works
                                       n, _ptr(out), _ptr(arr_offsets), _ptr(workspace), int(wb),
                                       ctypes.byref(o), _stream_handle(stream)),
            "eat_query_batch_multi")
+    return out
+
+
+def eat_query_batch_noalloc(net: Net, sources, times, out, stream=None, **opts):
+    """eat_query_batch for callers that cannot allocate device memory: no workspace argument,
+    the library's fixed 16 MiB scratch holds the frontier queues instead.  All buffers must be
+    device memory; calls that overlap on the GPU must be serialised (they share the scratch)."""
+    o = _opts(**opts)
+    _check(_lib.eat_query_batch_noalloc(net.handle, _ptr(sources), _ptr(times),
+                                        int(sources.shape[0]), _ptr(out), ctypes.byref(o),
+                                        _stream_handle(stream)), "eat_query_batch_noalloc")
     return out
 
 
