@@ -100,7 +100,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -111,6 +111,17 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first(self, timeout=5.0):
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.02)
+
+    def mark(self):
+        self.start = len(self.lines)
+
+    def stop_mark(self):
+        self.end = len(self.lines)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -124,7 +135,9 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        lo = getattr(self, "start", 0)
+        hi = max(getattr(self, "end", len(self.lines)), lo + 1)
+        for line in self.lines[lo:hi]:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue
@@ -246,18 +259,22 @@ def run_ours(args):
                             status=status[i], counters=cnt[i], **opts)
         b.record(stream)
 
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(dev) as clocks:
+        clocks.wait_first()
+        for i in range(args.warmup):
+            step(i)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.mark()
         t_wall = time.perf_counter()
         for i in range(args.warmup, n_steps):
             step(i)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+        time.sleep(0.06)
+        clocks.stop_mark()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -356,7 +373,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="city", choices=["city", "small", "large"])

@@ -90,6 +90,9 @@ typedef struct {
     int64_t n_ap;           /* AP records */
     int64_t n_cl;           /* cluster-offset entries */
     int64_t device_bytes;   /* bytes of the resident device copy */
+    int32_t k_min;          /* device layout: first cluster index stored */
+    int32_t y;              /* device layout: clusters stored per type (the paper's y) */
+    int64_t n_ap_extra;     /* device layout: APs beyond the two kept in a cluster entry */
 } eat_stats;
 
 /* Read-only host view of the built arrays (Section IV-A's CT[], CL[], AP[], in
@@ -111,18 +114,30 @@ typedef struct {
     const int32_t *type_cl;
     const int32_t *cl;
     const uint32_t *ap;
+    /* The device layout, derived from the arrays above (Section IV-A's CL stride y):
+     *   type_dev[4 * n_types]        {v, lambda, row_ptr[v], row_ptr[v+1]}
+     *   cluster_entries[8 * n_types * y]  entry (t, k) for cluster k_min + k:
+     *       {start0, sc0, start1, sc1, next, x, n, 0}: the cluster's n APs, the first
+     *       two inline (sc = difference << 16 | terms), the others at ap_extra[x ..];
+     *       next = first departure of the next non-empty cluster, EAT_INF if none
+     *   ap_extra[2 * n_ap_extra] */
+    const int32_t *type_dev;
+    const int32_t *cluster_entries;
+    const uint32_t *ap_extra;
 } eat_net_view;
 
 /* Per-query work counters (optional output of the query calls). */
 typedef struct {
     int64_t rounds;    /* relaxation rounds run (Algorithm 5's while loop) */
-    int64_t vertices;  /* active stops expanded, summed over rounds */
+    int64_t vertices;  /* active stops expanded, summed over rounds (a stop with no
+                          outgoing connection never needs expanding) */
     int64_t types;     /* connection types examined with an active tail: the
                           "connections processed" of Section V-C */
-    int64_t evals;     /* of those, types with a departure at or after e[u]
-                          (their e[v] is read) */
-    int64_t lookups;   /* of those, types whose cluster was searched (Section III-D) */
-    int64_t aps;       /* AP records read by the cluster lookup (Algorithm 6) */
+    int64_t evals;     /* of the looked-up types, those with a departure at or after
+                          e[u] (their e[v] is read) */
+    int64_t lookups;   /* of the examined types, those whose cluster entry was read
+                          (Section III-D); types >= lookups >= evals */
+    int64_t aps;       /* AP records examined by the cluster lookup (Algorithm 6) */
     int64_t relaxed;   /* successful lowerings of some e[v] (Algorithm 3) */
 } eat_counters;
 

@@ -53,8 +53,9 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct DeviceInfo {
     int sms = 0;
-    size_t smem_optin = 0;
-    size_t smem_static_reserve = 1024;  // static __shared__ of the kernel + margin
+    size_t smem_optin = 0;        // per block
+    size_t smem_per_sm = 0;
+    size_t reserve = 2048;        // static __shared__ of the kernel + per-block reservation
     bool init = false;
 };
 
@@ -73,13 +74,16 @@ static int device_info(int dev, DeviceInfo &out) {
         e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(smem optin)");
         d.smem_optin = (size_t)v;
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(smem per SM)");
+        d.smem_per_sm = (size_t)v;
         // Allow every CTA kernel the full opt-in shared memory (once per device).
         DeviceGuard guard(dev);
         for (int nets : {1, EAT_MAX_NETS})
             for (int mem = 0; mem < 3; ++mem) {
                 e = cudaFuncSetAttribute(cta_kernel(nets, mem),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(d.smem_optin - d.smem_static_reserve));
+                                         (int)(d.smem_optin - d.reserve));
                 if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
             }
         d.init = true;
@@ -88,21 +92,27 @@ static int device_info(int dev, DeviceInfo &out) {
     return EAT_OK;
 }
 
+// Launch plan of the CTA kernel for queries on networks of at most vmax stops.
 struct Plan {
-    int mem = 0;
+    int mem = 0;                  // 0 shared arrivals + bitmaps, 1 shared bitmaps, 2 none shared
     int block = 512;
     int vw_log2 = 3;
     int grid = 0;
-    size_t smem = 0;
+    size_t smem = 0;              // dynamic shared memory bytes
     int32_t vmax = 0;
-    int64_t queue_stride = 0;
-    int64_t mask_stride = 0;
+    int32_t qcap = 0;             // shared-memory (stop, type) items per buffer
+    int32_t mask_words = 0;       // words per bitmap
+    int32_t smem_mask_off = 0;    // int offsets into dynamic shared memory
+    int32_t smem_q_off = 0;
+    int64_t spill_stride = 0;     // ints per persistent block
+    int64_t mask_stride = 0;      // words per persistent block (global bitmaps only)
     size_t ws_bytes = 0;
-    size_t off_queues = 0, off_mask = 0;
+    size_t off_spill = 0, off_mask = 0;
     int nets = 1;
 };
 
 static constexpr size_t kWsHeader = 256;   // work counter + internal status / counters
+static constexpr size_t kQueueEntryBytes = 16;  // (stop, type) item x 2 buffers
 
 static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_query_opts *o,
                      Plan &p) {
@@ -119,28 +129,45 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     while ((1 << l) < vw) ++l;
     if ((1 << l) != vw || vw > 32) return fail(EAT_ERR_INVALID, "vwarp must be 1, 2, 4, 8, 16 or 32");
     p.vw_log2 = l;
-    const size_t words = ((size_t)vmax + 31) / 32;
-    const size_t arr_bytes = align_up((size_t)vmax, 4) * 4 + words * 4;
-    const size_t limit = d.smem_optin - d.smem_static_reserve;
+    if (o && o->mode != EAT_MODE_AUTO && o->mode != EAT_MODE_CTA)
+        return fail(EAT_ERR_INVALID, "mode must be EAT_MODE_AUTO or EAT_MODE_CTA");
     const int place = o ? o->placement : EAT_PLACE_AUTO;
     if (place < EAT_PLACE_AUTO || place > EAT_PLACE_GLOBAL)
         return fail(EAT_ERR_INVALID, "placement must be one of EAT_PLACE_*");
-    if (o && o->mode != EAT_MODE_AUTO && o->mode != EAT_MODE_CTA)
-        return fail(EAT_ERR_INVALID, "mode must be EAT_MODE_AUTO or EAT_MODE_CTA");
-    if (place == EAT_PLACE_SHARED && arr_bytes > limit)
+
+    const size_t words = ((size_t)vmax + 31) / 32;
+    p.mask_words = (int32_t)align_up(words, 4);
+    const size_t arr_bytes = align_up((size_t)vmax, 4) * 4;
+    const size_t mask_bytes = 2 * (size_t)p.mask_words * 4;
+    const size_t qmin = std::min<size_t>((size_t)std::max(vmax, 1), 256);
+    const size_t limit = d.smem_optin - d.reserve;
+    auto base = [&](int mem) { return (mem == 0 ? arr_bytes : 0) + (mem <= 1 ? mask_bytes : 0); };
+    auto fits = [&](int mem) { return base(mem) + kQueueEntryBytes * qmin <= limit; };
+    if (place == EAT_PLACE_SHARED && !fits(0))
         return fail(EAT_ERR_INVALID, "arrivals do not fit in shared memory");
-    if (place == EAT_PLACE_GLOBAL_ARR && words * 4 > limit)
-        return fail(EAT_ERR_INVALID, "bitmap does not fit in shared memory");
-    if (place == EAT_PLACE_SHARED || (place == EAT_PLACE_AUTO && arr_bytes <= limit)) {
-        p.mem = 0;
-        p.smem = arr_bytes;
-    } else if (place == EAT_PLACE_GLOBAL_ARR || (place == EAT_PLACE_AUTO && words * 4 <= limit)) {
-        p.mem = 1;
-        p.smem = words * 4;
-    } else {
-        p.mem = 2;
-        p.smem = 0;
+    if (place == EAT_PLACE_GLOBAL_ARR && !fits(1))
+        return fail(EAT_ERR_INVALID, "bitmaps do not fit in shared memory");
+    if (place == EAT_PLACE_SHARED || (place == EAT_PLACE_AUTO && fits(0))) p.mem = 0;
+    else if (place == EAT_PLACE_GLOBAL_ARR || (place == EAT_PLACE_AUTO && fits(1))) p.mem = 1;
+    else p.mem = 2;
+
+    // Largest queue capacity that keeps the most blocks per SM the threads allow.
+    const size_t b0 = base(p.mem);
+    const int max_blocks = std::max(1, 2048 / p.block);
+    p.qcap = (int32_t)qmin;
+    for (int b = max_blocks; b >= 1; --b) {
+        const size_t budget = std::min(limit, d.smem_per_sm / (size_t)b - d.reserve);
+        if (d.smem_per_sm / (size_t)b < d.reserve || b0 + kQueueEntryBytes * qmin > budget) continue;
+        size_t cap = (budget - b0) / kQueueEntryBytes;
+        cap = std::min(cap, (size_t)std::max(vmax, 1));
+        if (cap >= 64) cap &= ~(size_t)31;
+        p.qcap = (int32_t)std::max(cap, qmin);
+        break;
     }
+    p.smem_mask_off = p.mem == 0 ? (int32_t)(arr_bytes / 4) : 0;
+    p.smem_q_off = p.smem_mask_off + (p.mem <= 1 ? 2 * p.mask_words : 0);
+    p.smem = (size_t)p.smem_q_off * 4 + kQueueEntryBytes * (size_t)p.qcap;
+
     int per_sm = 0;
     cudaError_t e;
     {
@@ -151,12 +178,42 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) return fail(EAT_ERR_INVALID, "kernel does not fit on an SM with this block size");
     p.grid = (int)std::min<int64_t>((int64_t)std::max(n, 1), (int64_t)per_sm * d.sms);
-    p.queue_stride = (int64_t)align_up((size_t)vmax * 2, 64);
-    p.mask_stride = p.mem == 2 ? (int64_t)align_up(words, 64) : 0;
-    p.off_queues = kWsHeader;
-    p.off_mask = p.off_queues + (size_t)p.grid * (size_t)p.queue_stride * 4;
+    p.spill_stride = (int64_t)align_up((size_t)vmax * 2, 64);
+    p.mask_stride = p.mem == 2 ? (int64_t)align_up(2 * (size_t)p.mask_words, 64) : 0;
+    p.off_spill = kWsHeader;
+    p.off_mask = p.off_spill + (size_t)p.grid * (size_t)p.spill_stride * 4;
     p.ws_bytes = p.off_mask + (size_t)p.grid * (size_t)p.mask_stride * 4;
     return EAT_OK;
+}
+
+// Kernel arguments for a plan; `grid` persistent blocks share the scratch at `ws`.
+static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net_idx,
+                           const int32_t *src, const int32_t *ts, int32_t n, int n_nets,
+                           int32_t *arr_out, const int64_t *arr_off, int32_t max_rounds,
+                           int32_t *status, eat_counters *counters) {
+    QueryArgs qa;
+    qa.net_idx = net_idx;
+    qa.src = src;
+    qa.ts = ts;
+    qa.arr_off = arr_off;
+    qa.arr_out = arr_out;
+    qa.spill = (int32_t *)(ws + kWsHeader);
+    qa.gmask = (uint32_t *)(ws + kWsHeader + (size_t)grid * (size_t)p.spill_stride * 4);
+    qa.work = (int32_t *)ws;
+    qa.status = status;
+    qa.counters = counters;
+    qa.spill_stride = p.spill_stride;
+    qa.mask_stride = p.mask_stride;
+    qa.n = n;
+    qa.n_nets = n_nets;
+    qa.max_rounds = max_rounds;
+    qa.vw_log2 = p.vw_log2;
+    qa.vmax = p.vmax;
+    qa.qcap = p.qcap;
+    qa.mask_words = p.mask_words;
+    qa.smem_mask_off = p.smem_mask_off;
+    qa.smem_q_off = p.smem_q_off;
+    return qa;
 }
 
 static int ensure_buffer(void *&buf, size_t &cap, size_t need) {
@@ -189,25 +246,10 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
         return fail(EAT_ERR_WORKSPACE, "workspace of " + std::to_string(ws_bytes) +
                                            " bytes, need " + std::to_string(p.ws_bytes));
     if (n == 0) return EAT_OK;
-    char *w = (char *)ws;
-    QueryArgs qa;
-    qa.net_idx = net_idx;
-    qa.src = src;
-    qa.ts = ts;
-    qa.arr_off = arr_off;
-    qa.arr_out = arr_out;
-    qa.queues = (int32_t *)(w + p.off_queues);
-    qa.gmask = (uint32_t *)(w + p.off_mask);
-    qa.work = (int32_t *)w;
-    qa.status = status_override ? status_override : (o ? o->status : nullptr);
-    qa.counters = counters_override ? counters_override : (o ? o->counters : nullptr);
-    qa.queue_stride = p.queue_stride;
-    qa.mask_stride = p.mask_stride;
-    qa.n = n;
-    qa.n_nets = n_nets;
-    int32_t cap = (o && o->max_rounds > 0) ? o->max_rounds : (vmax < INT32_MAX ? vmax + 1 : vmax);
-    qa.max_rounds = cap;
-    qa.vw_log2 = p.vw_log2;
+    const int32_t cap = (o && o->max_rounds > 0) ? o->max_rounds : (vmax < INT32_MAX ? vmax + 1 : vmax);
+    QueryArgs qa = make_args(p, p.grid, (char *)ws, net_idx, src, ts, n, n_nets, arr_out, arr_off,
+                             cap, status_override ? status_override : (o ? o->status : nullptr),
+                             counters_override ? counters_override : (o ? o->counters : nullptr));
     DeviceGuard guard(dev);
     cudaError_t e = cudaMemsetAsync(qa.work, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -239,6 +281,7 @@ int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net *
     eat_net *net = new (std::nothrow) eat_net();
     if (!net) return fail(EAT_ERR_OOM, "host allocation failed");
     int rc = build_host(conn, width, o.t0, net->host);
+    if (!rc) rc = build_fused(net->host);
     if (rc) {
         delete net;
         return rc;
@@ -255,11 +298,9 @@ int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net *
         const HostNet &h = net->host;
         size_t off_row = 0;
         size_t off_ty = align_up(off_row + ((size_t)h.n_stops + 1) * 4, 256);
-        size_t off_clb = align_up(off_ty + (size_t)h.n_types * 16, 256);
-        size_t off_cl = align_up(off_clb + (size_t)h.n_types * 4, 256);
-        size_t off_ap = align_up(off_cl + h.cl.size() * 4, 256);
-        // One spare AP-sized word pair so that no read can run past the blob.
-        size_t total = align_up(off_ap + h.ap.size() * 4 + 16, 256);
+        size_t off_ce = align_up(off_ty + h.ty_dev.size() * 4, 256);
+        size_t off_apx = align_up(off_ce + h.ce.size() * 4, 256);
+        size_t total = align_up(off_apx + h.apx.size() * 4 + 16, 256);
         DeviceGuard guard(o.device);
         if (!guard.ok) {
             delete net;
@@ -275,10 +316,9 @@ int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net *
         char *b = (char *)net->blob;
         struct Piece { size_t off; const void *src; size_t bytes; } pieces[] = {
             {off_row, h.row_ptr.data(), h.row_ptr.size() * 4},
-            {off_ty, h.type_rec.data(), h.type_rec.size() * 4},
-            {off_clb, h.type_cl.data(), h.type_cl.size() * 4},
-            {off_cl, h.cl.data(), h.cl.size() * 4},
-            {off_ap, h.ap.data(), h.ap.size() * 4},
+            {off_ty, h.ty_dev.data(), h.ty_dev.size() * 4},
+            {off_ce, h.ce.data(), h.ce.size() * 4},
+            {off_apx, h.apx.data(), h.apx.size() * 4},
         };
         for (const Piece &pc : pieces) {
             if (!pc.bytes) continue;
@@ -292,13 +332,14 @@ int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net *
         NetDev &d = net->dev;
         d.row_ptr = (const int32_t *)(b + off_row);
         d.ty = (const int4 *)(b + off_ty);
-        d.cl_base = (const int32_t *)(b + off_clb);
-        d.cl = (const int32_t *)(b + off_cl);
-        d.ap = (const uint2 *)(b + off_ap);
+        d.ce = (const int4 *)(b + off_ce);
+        d.apx = (const uint2 *)(b + off_apx);
         d.n_stops = h.n_stops;
         d.n_types = h.n_types;
         d.t0 = h.t0;
         d.width = h.width;
+        d.k_min = h.k_min;
+        d.y = h.y;
     }
     *out = net;
     return EAT_OK;
@@ -331,6 +372,9 @@ int eat_get_stats(const eat_net *net, eat_stats *out) {
     out->n_ap = (int64_t)h.ap.size() / 2;
     out->n_cl = (int64_t)h.cl.size();
     out->device_bytes = net->blob_bytes;
+    out->k_min = h.k_min;
+    out->y = h.y;
+    out->n_ap_extra = (int64_t)h.apx.size() / 2;
     return EAT_OK;
 }
 
@@ -342,6 +386,9 @@ int eat_net_host_view(const eat_net *net, eat_net_view *out) {
     out->type_cl = net->host.type_cl.data();
     out->cl = net->host.cl.data();
     out->ap = net->host.ap.data();
+    out->type_dev = net->host.ty_dev.data();
+    out->cluster_entries = net->host.ce.data();
+    out->ap_extra = net->host.apx.data();
     return EAT_OK;
 }
 
@@ -600,8 +647,8 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     Plan p;
     int rc = make_plan(net->device, net->host.n_stops, n, 1, opts, p);
     if (rc) return rc;
-    // Fewer persistent blocks so that their queues fit the fixed scratch.
-    const size_t per_block = (size_t)p.queue_stride * 4 + (size_t)p.mask_stride * 4;
+    // Fewer persistent blocks so that their queue spill fits the fixed scratch.
+    const size_t per_block = (size_t)p.spill_stride * 4 + (size_t)p.mask_stride * 4;
     const size_t fit = (EAT_NOALLOC_SCRATCH_BYTES - kWsHeader) / per_block;
     if (fit < 1)
         return fail(EAT_ERR_INVALID, "network too large for the no-allocation scratch");
@@ -609,24 +656,10 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     void *scratch = nullptr;
     rc = noalloc_scratch(net->device, &scratch);
     if (rc) return rc;
-    char *w = (char *)scratch;
-    QueryArgs qa;
-    qa.net_idx = nullptr;
-    qa.src = sources;
-    qa.ts = times;
-    qa.arr_off = nullptr;
-    qa.arr_out = arr_out;
-    qa.queues = (int32_t *)(w + kWsHeader);
-    qa.gmask = (uint32_t *)(w + kWsHeader + (size_t)grid * (size_t)p.queue_stride * 4);
-    qa.work = (int32_t *)w;
-    qa.status = opts ? opts->status : nullptr;
-    qa.counters = opts ? opts->counters : nullptr;
-    qa.queue_stride = p.queue_stride;
-    qa.mask_stride = p.mask_stride;
-    qa.n = n;
-    qa.n_nets = 1;
-    qa.max_rounds = (opts && opts->max_rounds > 0) ? opts->max_rounds : net->host.n_stops + 1;
-    qa.vw_log2 = p.vw_log2;
+    const int32_t cap = (opts && opts->max_rounds > 0) ? opts->max_rounds : net->host.n_stops + 1;
+    QueryArgs qa = make_args(p, grid, (char *)scratch, nullptr, sources, times, n, 1, arr_out,
+                             nullptr, cap, opts ? opts->status : nullptr,
+                             opts ? opts->counters : nullptr);
     cudaStream_t st = (cudaStream_t)stream;
     // The query counter must start at zero; the queues need no clearing.
     cudaError_t e = cudaMemsetAsync(qa.work, 0, sizeof(int32_t), st);

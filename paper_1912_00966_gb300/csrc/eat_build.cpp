@@ -277,4 +277,92 @@ int build_host(const eat_connections *c, int32_t width, int32_t t0, HostNet &h) 
     return EAT_OK;
 }
 
+// Device layout (see NetDev in eat_internal.h): one 32-byte entry per (type,
+// cluster) for every cluster of the network, with the cluster's first two APs
+// inline, the index of its further APs, and the first departure of the next
+// non-empty cluster, so one load of the entry answers getConnection for most
+// clusters (Algorithm 6 inside the hourly cluster of Section III-D).
+int build_fused(HostNet &h) {
+    const int32_t T = h.n_types, W = h.width, t0 = h.t0;
+    int32_t kmin = INT32_MAX, kmax = INT32_MIN;
+    for (int32_t t = 0; t < T; ++t) {
+        kmin = std::min(kmin, (h.type_rec[4 * (size_t)t + 2] - t0) / W);
+        kmax = std::max(kmax, (h.type_rec[4 * (size_t)t + 3] - t0) / W);
+    }
+    if (T == 0) kmin = kmax = 0;
+    const int64_t Y = (int64_t)kmax - kmin + 1;
+    if ((int64_t)T * Y * 32 > ((int64_t)64 << 30))
+        return fail(EAT_ERR_INVALID, "cluster table of " + std::to_string(T) + " types x " +
+                                         std::to_string(Y) + " clusters is too large; use a wider cluster_width");
+    h.k_min = kmin;
+    h.y = (int32_t)Y;
+    std::vector<int64_t> xoff((size_t)T + 1, 0);
+    for (int32_t t = 0; t < T; ++t) {
+        const int32_t kf = (h.type_rec[4 * (size_t)t + 2] - t0) / W;
+        const int32_t kl = (h.type_rec[4 * (size_t)t + 3] - t0) / W;
+        const int32_t b = h.type_cl[t];
+        int64_t extra = 0;
+        for (int32_t k = kf; k <= kl; ++k) extra += std::max(0, h.cl[b + k + 1] - h.cl[b + k] - 2);
+        xoff[t + 1] = xoff[t] + extra;
+    }
+    if (xoff[T] >= INT32_MAX) return fail(EAT_ERR_INVALID, "too many APs for 32-bit indices");
+    try {
+        h.ty_dev.resize((size_t)T * 4);
+        h.ce.assign((size_t)T * (size_t)Y * 8, 0);
+        h.apx.resize((size_t)xoff[T] * 2);
+    } catch (const std::bad_alloc &) {
+        return fail(EAT_ERR_OOM, "host allocation of the cluster table failed");
+    }
+    auto fill = [&](int32_t t_begin, int32_t t_end) {
+        for (int32_t t = t_begin; t < t_end; ++t) {
+            const int32_t v = h.type_rec[4 * (size_t)t], lam = h.type_rec[4 * (size_t)t + 1];
+            int32_t *ty = &h.ty_dev[4 * (size_t)t];
+            ty[0] = v;
+            ty[1] = lam;
+            ty[2] = h.row_ptr[v];
+            ty[3] = h.row_ptr[v + 1];
+            const int32_t kf = (h.type_rec[4 * (size_t)t + 2] - t0) / W;
+            const int32_t kl = (h.type_rec[4 * (size_t)t + 3] - t0) / W;
+            const int32_t b = h.type_cl[t];
+            int64_t x = xoff[t];
+            int32_t *row = &h.ce[(size_t)t * (size_t)Y * 8];
+            for (int32_t kr = 0; kr < Y; ++kr) {
+                int32_t *e = row + (size_t)kr * 8;
+                const int32_t k = kmin + kr;
+                int32_t lo = 0, n = 0;
+                if (k >= kf && k <= kl) {
+                    lo = h.cl[b + k];
+                    n = h.cl[b + k + 1] - lo;
+                }
+                e[0] = n >= 1 ? (int32_t)h.ap[2 * (size_t)lo] : EAT_INF;
+                e[1] = n >= 1 ? (int32_t)h.ap[2 * (size_t)lo + 1] : 0;
+                e[2] = n >= 2 ? (int32_t)h.ap[2 * (size_t)(lo + 1)] : EAT_INF;
+                e[3] = n >= 2 ? (int32_t)h.ap[2 * (size_t)(lo + 1) + 1] : 0;
+                e[5] = (int32_t)x;
+                e[6] = n;
+                for (int32_t j = 2; j < n; ++j, ++x) {
+                    h.apx[2 * (size_t)x] = h.ap[2 * (size_t)(lo + j)];
+                    h.apx[2 * (size_t)x + 1] = h.ap[2 * (size_t)(lo + j) + 1];
+                }
+            }
+            int32_t next = EAT_INF;
+            for (int32_t kr = (int32_t)Y - 1; kr >= 0; --kr) {
+                int32_t *e = row + (size_t)kr * 8;
+                e[4] = next;
+                if (e[6] > 0) next = e[0];
+            }
+        }
+    };
+    unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    const int32_t per = (T + (int32_t)hw - 1) / (int32_t)hw;
+    for (unsigned i = 1; i < hw; ++i) {
+        const int32_t a = std::min(T, (int32_t)i * per), z = std::min(T, (int32_t)(i + 1) * per);
+        if (a < z) th.emplace_back(fill, a, z);
+    }
+    fill(0, std::min(T, per));
+    for (auto &t : th) t.join();
+    return EAT_OK;
+}
+
 }  // namespace eat

@@ -15,16 +15,30 @@
 namespace eat {
 
 // Device-side descriptor of one resident network (plain pointers into one blob).
+//
+// Device layout (derived from the logical arrays of HostNet by build_fused):
+//   ty[t]              int4 {v, lambda, row_ptr[v], row_ptr[v+1]} -- the head stop's
+//                      row range travels with the type, so a stop pushed onto the
+//                      frontier needs no further lookup to be expanded
+//   ce[t*y + k]        32-byte cluster entry of type t for cluster k_min + k, for every
+//                      cluster of the network (the paper's dense CL stride y):
+//                        int4 {start0, sc0, start1, sc1}   first two APs inline
+//                        int4 {next, x, n, 0}              next = first departure of the
+//                                                          next non-empty cluster (INF if
+//                                                          none), APs 3..n at apx[x ..]
+//                      sc = (difference << 16) | number of terms
+//   apx[]              uint2 {first term, sc} of the third and later APs of a cluster
 struct NetDev {
     const int32_t *row_ptr;   // [V + 1] types by tail stop
-    const int4 *ty;           // [T] {v, lambda, first departure, last departure}
-    const int32_t *cl_base;   // [T] cluster k of type t starts at cl[cl_base[t] + k]
-    const int32_t *cl;        // [n_cl]
-    const uint2 *ap;          // [n_ap] {first term, (difference << 16) | terms}
+    const int4 *ty;           // [T]
+    const int4 *ce;           // [2 * T * y]
+    const uint2 *apx;         // [n_apx]
     int32_t n_stops;
     int32_t n_types;
     int32_t t0;
     int32_t width;            // cluster width (seconds)
+    int32_t k_min;            // first cluster index stored
+    int32_t y;                // clusters stored per type
 };
 
 // Up to NETS networks passed by value as a kernel parameter.
@@ -43,6 +57,11 @@ struct HostNet {
     std::vector<int32_t> type_cl;    // T
     std::vector<int32_t> cl;         // n_cl
     std::vector<uint32_t> ap;        // 2 n_ap
+    // Device layout (see NetDev).
+    int32_t k_min = 0, y = 1;
+    std::vector<int32_t> ty_dev;     // 4 T
+    std::vector<int32_t> ce;         // 8 T y
+    std::vector<uint32_t> apx;       // 2 n_apx
 };
 
 }  // namespace eat
@@ -69,6 +88,9 @@ void clear_error();
 
 // Host preprocessing (eat_build.cpp): fills `h` from the connections.
 int build_host(const eat_connections *c, int32_t width, int32_t t0, HostNet &h);
+
+// Device layout from the logical arrays (eat_build.cpp).
+int build_fused(HostNet &h);
 
 // Greedy AP cover of sorted unique values (eat_build.cpp); appends (first, step, terms).
 void ap_cover(const int32_t *vals, int32_t n, int32_t width_hint,

@@ -4,65 +4,90 @@
 //   init     e[] = INF, e[s] = t_s, frontier = {s}                 (Algorithm 2)
 //   round    for every stop u of the frontier and every connection type
 //            (u, v, lambda) leaving u: find the first departure t_c >= e[u]
-//            (clusters + APs, Algorithm 6), and if t_c + lambda < e[v] lower
-//            e[v] with atomicMin and put v on the next frontier     (Algorithm 3)
+//            (the APs of e[u]'s cluster, else the next non-empty cluster;
+//            Algorithm 6), and if t_c + lambda < e[v] lower e[v] with atomicMin
+//            and put v on the next frontier                        (Algorithm 3)
 //   stop     when a round puts nobody on the next frontier.
 // The frontier replaces the paper's active[]/nextactive[] flags (Section IV-B):
 // a stop joins the next frontier only after its e[] was lowered, through a
-// test-and-set on a per-query bitmap, so each stop appears at most once per
+// test-and-set on a per-round bitmap, so each stop appears at most once per
 // round; atomicMin resolves concurrent lowerings (Section IV-C).
 //
 // CTA mode: one thread block owns one query at a time (persistent blocks take
-// queries from an atomic counter).  Rounds are separated by block barriers, so
-// there is no grid-wide synchronisation and no spin-wait anywhere.  The arrival
-// row lives in shared memory when it fits (SMEM_ARR), otherwise in the output
-// row in global memory; the bitmap lives in shared memory when it fits.
+// queries from an atomic counter), so rounds are separated by one block barrier
+// and there is no grid-wide synchronisation and no spin-wait anywhere.
+//
+// Work items: when a stop v joins the next frontier, the thread that lowered e[v]
+// writes one (v, type) item per connection type leaving v into shared memory, so
+// the next round hands every thread one (stop, type) pair: the paper's one thread
+// per connection type (Algorithm 5), restricted to the active tails.  Per item the
+// dependent memory chain is one L2 round trip: the type record and its 32-byte
+// cluster entry are independent loads (the entry's address depends only on the
+// type and e[u]'s cluster); e[u], e[v] and the frontier live in shared memory.
+// Stops whose items do not fit spill to a global queue and are expanded by
+// `vwarp`-lane sub-warps (Section III-F's virtual warps).
+//
+// Buffers per query: arrivals in shared memory when they fit (SMEM_ARR), else
+// the output row; two frontier bitmaps (this round's pushes, last round's) in
+// shared memory when they fit (SMEM_MASK).
 #include <cuda_runtime.h>
 
 #include "eat_launch.h"
 
 namespace eat {
 
-constexpr int kInf = INT32_MAX;
+constexpr int32_t kInf = INT32_MAX;
 
-
-// Least departure >= e of a type whose first departure is < e and last is >= e:
-// scan the APs of e's cluster (Algorithm 6, restricted to one cluster as in
-// Section III-D); if that cluster has no departure >= e, the first AP of the
-// next non-empty cluster starts with the answer.
-__device__ __forceinline__ int32_t cluster_ap_lookup(const NetDev &N, int32_t cl_base, int32_t e,
-                                                     int32_t &aps) {
-    const int32_t k = (e - N.t0) / N.width;
-    const int32_t lo = __ldg(N.cl + cl_base + k);
-    const int32_t hi = __ldg(N.cl + cl_base + k + 1);
-    int32_t tc = kInf;
-    for (int32_t a = lo; a < hi; ++a) {
-        const uint2 r = __ldg(N.ap + a);
-        ++aps;
-        const int32_t start = (int32_t)r.x;
-        if (start >= tc) break;              // APs are ordered by first term
-        if (e <= start) { tc = start; break; }
-        const int32_t step = (int32_t)(r.y >> 16);
-        const int32_t last = start + ((int32_t)(r.y & 0xffffu) - 1) * step;
-        if (e <= last) {                      // start < e <= last: step >= 1
-            const int32_t i = (e - start + step - 1) / step;
-            tc = min(tc, start + i * step);
-        }
-    }
-    if (tc == kInf) {
-        tc = (int32_t)__ldg(N.ap + hi).x;
-        ++aps;
-    }
-    return tc;
+// Least term >= e of the AP {start, sc = difference << 16 | terms}, or kInf.
+__device__ __forceinline__ int32_t ap_candidate(int32_t start, uint32_t sc, int32_t e) {
+    if (e <= start) return start;
+    const int32_t step = (int32_t)(sc >> 16);
+    const int32_t last = start + ((int32_t)(sc & 0xffffu) - 1) * step;
+    if (e > last) return kInf;                 // also every one-term AP
+    return start + ((e - start + step - 1) / step) * step;
 }
 
-// getConnection for type t at time e: least departure >= e, or kInf.
+// getConnectionFromAPs (Algorithm 6) over the APs of one cluster entry, with the
+// Cluster-AP fallback of Section III-D: if the cluster has no departure >= e, the
+// answer is the first departure of the next non-empty cluster (`next`).
+// c0 = {start0, sc0, start1, sc1}, c1 = {next, x, n, 0}.
+__device__ __forceinline__ int32_t cluster_lookup(const int4 c0, const int4 c1, int32_t e,
+                                                  const uint2 *__restrict__ apx, int32_t &aps) {
+    const int32_t n = c1.z;
+    int32_t tc = kInf;
+    if (n > 0) {
+        ++aps;
+        tc = ap_candidate(c0.x, (uint32_t)c0.y, e);
+        if (n > 1 && c0.z < tc) {             // APs are ordered by first term
+            ++aps;
+            tc = min(tc, ap_candidate(c0.z, (uint32_t)c0.w, e));
+            for (int32_t j = 2; j < n; ++j) {
+                const uint2 r = __ldg(apx + c1.y + (j - 2));
+                if ((int32_t)r.x >= tc) break;
+                ++aps;
+                tc = min(tc, ap_candidate((int32_t)r.x, r.y, e));
+            }
+        }
+    }
+    return tc == kInf ? c1.x : tc;
+}
+
+// Cluster slot of time e relative to the first stored cluster; e before the first
+// cluster maps to slot 0 (every departure is then >= e), and a result >= y means
+// no departure at or after e exists in the network.
+__device__ __forceinline__ int32_t cluster_slot(const NetDev &N, int32_t e) {
+    const int64_t d = (int64_t)e - N.t0;
+    const int32_t k = d < 0 ? 0 : (int32_t)((uint32_t)d / (uint32_t)N.width) - N.k_min;
+    return k < 0 ? 0 : k;
+}
+
+// getConnection of type t at time e: least departure >= e, or kInf.
 __device__ __forceinline__ int32_t next_departure(const NetDev &N, int32_t t, int32_t e,
                                                   int32_t &aps) {
-    const int4 ty = __ldg(N.ty + t);
-    if (e > ty.w) return kInf;
-    if (e <= ty.z) return ty.z;
-    return cluster_ap_lookup(N, __ldg(N.cl_base + t), e, aps);
+    const int32_t k = cluster_slot(N, e);
+    if (k >= N.y) return kInf;
+    const int4 *c = N.ce + 2 * ((int64_t)t * N.y + k);
+    return cluster_lookup(__ldg(c), __ldg(c + 1), e, N.apx, aps);
 }
 
 template <bool SMEM_ARR>
@@ -71,12 +96,16 @@ __device__ __forceinline__ int32_t load_arr(const int32_t *arr, int32_t i) {
     return __ldcg(arr + i);
 }
 
+constexpr int32_t kNullItem = -1;           // hole left by a stop that spilled
+constexpr int32_t kFirstItem = INT32_MIN;    // flag on the first item of a stop
+
 template <int NETS, bool SMEM_ARR, bool SMEM_MASK>
 __global__ void __launch_bounds__(1024, 1)
 eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) {
     extern __shared__ __align__(16) int32_t smem[];
     __shared__ int32_t s_q;
-    __shared__ int32_t s_tail[2];
+    __shared__ int32_t s_items[3];    // items reserved per round (rotating)
+    __shared__ int32_t s_spill[3];    // stops spilled per round (rotating)
     __shared__ unsigned long long s_cnt[6];
 
     const int tid = threadIdx.x;
@@ -85,7 +114,13 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
     const int lane = tid & (vw - 1);
     const int sub = tid >> qa.vw_log2;
     const int nsub = nthr >> qa.vw_log2;
-    int32_t *const q_base = qa.queues + (int64_t)blockIdx.x * qa.queue_stride;
+    const int32_t icap = qa.qcap;
+
+    // Item buffers (stop, type) and spill queues; round r writes buffer r & 1.
+    int32_t *const item_base = smem + qa.smem_q_off;
+    int32_t *const spill_base = qa.spill + (int64_t)blockIdx.x * qa.spill_stride;
+    uint32_t *const mask_base = SMEM_MASK ? (uint32_t *)(smem + qa.smem_mask_off)
+                                          : qa.gmask + (int64_t)blockIdx.x * qa.mask_stride;
 
     for (;;) {
         if (tid == 0) s_q = atomicAdd(qa.work, 1);
@@ -101,78 +136,128 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
         const int64_t off = qa.arr_off ? __ldg(qa.arr_off + q) : (int64_t)q * V;
         int32_t *const out = qa.arr_out + off;
         int32_t *const arr = SMEM_ARR ? smem : out;
-        const int32_t vpad = (V + 3) & ~3;
-        uint32_t *const mask = SMEM_MASK ? (uint32_t *)(SMEM_ARR ? smem + vpad : smem)
-                                         : qa.gmask + (int64_t)blockIdx.x * qa.mask_stride;
         const int32_t nwords = (V + 31) >> 5;
-        int32_t *qa_ = q_base;
-        int32_t *qb_ = q_base + V;
+        uint32_t *const mask0 = mask_base;
+        uint32_t *const mask1 = mask_base + qa.mask_words;
 
         // Algorithm 2: every stop passive at infinity.
         for (int32_t i = tid; i < V; i += nthr) arr[i] = kInf;
-        for (int32_t i = tid; i < nwords; i += nthr) mask[i] = 0u;
-        if (tid == 0) { s_tail[0] = 0; s_tail[1] = 0; }
+        for (int32_t i = tid; i < nwords; i += nthr) {
+            mask0[i] = 0u;
+            mask1[i] = 0u;
+        }
+        if (tid < 3) {
+            s_items[tid] = 0;
+            s_spill[tid] = 0;
+        }
         const int32_t s = __ldg(qa.src + q);
         const int32_t t_s = __ldg(qa.ts + q);
         const bool valid = net_ok && (unsigned)s < (unsigned)V;
         __syncthreads();
+        // The source is the frontier of "round -1": spill queue of buffer 1, counter slot 2.
         if (tid == 0 && valid) {
             arr[s] = t_s;
-            qa_[0] = s;
+            spill_base[qa.vmax] = s;
+            s_spill[2] = 1;
         }
         __syncthreads();
 
-        int32_t F = valid ? 1 : 0;
+        int32_t n_items = 0, n_spill = valid ? 1 : 0;
         int32_t rounds = 0;
-        int p = 0;
+        int cs = 0;                                       // counter slot written this round
         int32_t c_vert = 0, c_types = 0, c_evals = 0, c_lookups = 0, c_aps = 0, c_relax = 0;
-        while (F > 0 && rounds < qa.max_rounds) {
-            // The stops of this frontier may join the next one again.
-            for (int32_t i = tid; i < F; i += nthr) {
-                const int32_t u = __ldcg(qa_ + i);
-                atomicAnd(mask + (u >> 5), ~(1u << (u & 31)));
+        while (n_items + n_spill > 0 && rounds < qa.max_rounds) {
+            const int wr = rounds & 1, rd = wr ^ 1;
+            int32_t *const iu_rd = item_base + (2 * rd) * icap;
+            int32_t *const it_rd = iu_rd + icap;
+            int32_t *const iu_wr = item_base + (2 * wr) * icap;
+            int32_t *const it_wr = iu_wr + icap;
+            const int32_t *const sp_rd = spill_base + (int64_t)rd * qa.vmax;
+            int32_t *const sp_wr = spill_base + (int64_t)wr * qa.vmax;
+            uint32_t *const pmask = wr ? mask1 : mask0;    // stops pushed this round
+            uint32_t *const cmask = wr ? mask0 : mask1;    // stops pushed last round
+            // The slot used next round was last read two barriers ago.
+            if (tid == 0) {
+                const int nx = cs == 2 ? 0 : cs + 1;
+                s_items[nx] = 0;
+                s_spill[nx] = 0;
             }
-            __syncthreads();
-            for (int32_t i = sub; i < F; i += nsub) {
-                const int32_t u = __ldcg(qa_ + i);
+
+            // Relax type t of tail u (Algorithm 3 with getConnection, Algorithm 6);
+            // on success v joins the next frontier as items or as a spilled stop.
+            auto relax = [&](int32_t e_u, int32_t k, int32_t t) {
+                ++c_types;
+                ++c_lookups;
+                const int4 ty = __ldg(N.ty + t);            // {v, lambda, row of v}
+                const int4 *c = N.ce + 2 * ((int64_t)t * N.y + k);
+                const int32_t tc = cluster_lookup(__ldg(c), __ldg(c + 1), e_u, N.apx, c_aps);
+                if (tc == kInf) return;                     // no departure left (Section IV-D)
+                ++c_evals;
+                const int32_t v = ty.x;
+                const int32_t cand = tc + ty.y;
+                if (cand >= load_arr<SMEM_ARR>(arr, v)) return;
+                const int32_t old = atomicMin(arr + v, cand);
+                if (cand >= old) return;
+                ++c_relax;
+                const int32_t d = ty.w - ty.z;              // types leaving v
+                if (d <= 0) return;
+                const uint32_t bit = 1u << (v & 31);
+                if (atomicOr(pmask + (v >> 5), bit) & bit) return;   // already queued
+                const int32_t base = atomicAdd(&s_items[cs], d);
+                if (base + d <= icap) {
+                    iu_wr[base] = v | kFirstItem;
+                    it_wr[base] = ty.z;
+                    for (int32_t j = 1; j < d; ++j) {
+                        iu_wr[base + j] = v;
+                        it_wr[base + j] = ty.z + j;
+                    }
+                } else {
+                    for (int32_t j = base; j < icap; ++j) iu_wr[j] = kNullItem;
+                    sp_wr[atomicAdd(&s_spill[cs], 1)] = v;
+                }
+            };
+
+            // One thread per (stop, type) item.
+            for (int32_t i = tid; i < n_items; i += nthr) {
+                const int32_t raw = iu_rd[i];
+                if (raw == kNullItem) continue;
+                const int32_t u = raw & 0x7fffffff;
+                if (raw < 0) {                              // first item of u
+                    atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
+                    ++c_vert;
+                }
                 const int32_t e_u = load_arr<SMEM_ARR>(arr, u);
+                const int32_t k = cluster_slot(N, e_u);
+                if (k >= N.y) {                             // no departure left anywhere
+                    ++c_types;
+                    continue;
+                }
+                relax(e_u, k, it_rd[i]);
+            }
+            // Spilled stops: `vw` lanes per stop stride over its types.
+            for (int32_t i = sub; i < n_spill; i += nsub) {
+                const int32_t u = __ldcg(sp_rd + i);
                 const int32_t beg = __ldg(N.row_ptr + u);
                 const int32_t end = __ldg(N.row_ptr + u + 1);
-                c_vert += (lane == 0);
-                for (int32_t t = beg + lane; t < end; t += vw) {
-                    ++c_types;
-                    const int4 ty = __ldg(N.ty + t);   // {v, lambda, first, last}
-                    if (e_u > ty.w) continue;           // no departure left (Section IV-D)
-                    const int32_t v = ty.x, lam = ty.y;
-                    ++c_evals;
-                    const int32_t e_v = load_arr<SMEM_ARR>(arr, v);
-                    if (max(e_u, ty.z) + lam >= e_v) continue;   // cannot improve e[v]
-                    int32_t tc = ty.z;
-                    if (e_u > ty.z) {
-                        ++c_lookups;
-                        tc = cluster_ap_lookup(N, __ldg(N.cl_base + t), e_u, c_aps);
-                    }
-                    const int32_t cand = tc + lam;
-                    if (cand < e_v) {
-                        const int32_t old = atomicMin(arr + v, cand);
-                        if (cand < old) {
-                            ++c_relax;
-                            const uint32_t bit = 1u << (v & 31);
-                            if (!(atomicOr(mask + (v >> 5), bit) & bit)) {
-                                const int32_t pos = atomicAdd(&s_tail[p], 1);
-                                qb_[pos] = v;
-                            }
-                        }
-                    }
+                if (lane == 0) {
+                    atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
+                    ++c_vert;
                 }
+                const int32_t e_u = load_arr<SMEM_ARR>(arr, u);
+                const int32_t k = cluster_slot(N, e_u);
+                if (k >= N.y) {
+                    if (lane == 0) c_types += end - beg;
+                    continue;
+                }
+                for (int32_t t = beg + lane; t < end; t += vw) relax(e_u, k, t);
             }
             __syncthreads();
-            F = s_tail[p];
-            if (tid == 0) s_tail[p ^ 1] = 0;
-            int32_t *tmp = qa_; qa_ = qb_; qb_ = tmp;
-            p ^= 1;
+            n_items = min(s_items[cs], icap);
+            n_spill = s_spill[cs];
+            cs = cs == 2 ? 0 : cs + 1;
             ++rounds;
         }
+        const int32_t F = n_items + n_spill;
 
         if (SMEM_ARR) {
             __syncthreads();
@@ -185,11 +270,11 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                                        (unsigned long long)c_evals, (unsigned long long)c_lookups,
                                        (unsigned long long)c_aps, (unsigned long long)c_relax};
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
-                for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_down_sync(0xffffffffu, c[k], o);
+            for (int j = 0; j < 6; ++j)
+                for (int o = 16; o > 0; o >>= 1) c[j] += __shfl_down_sync(0xffffffffu, c[j], o);
             if ((tid & 31) == 0) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) atomicAdd(&s_cnt[k], c[k]);
+                for (int j = 0; j < 6; ++j) atomicAdd(&s_cnt[j], c[j]);
             }
             __syncthreads();
             if (tid == 0) {
@@ -219,13 +304,11 @@ __global__ void eat_next_departure_kernel(const NetDev N, const int32_t *types,
 
 // ------------------------------------------------------------------ launchers
 
-enum MemKind { kArrSmem = 0, kArrGlobalMaskSmem = 1, kArrGlobalMaskGlobal = 2 };
-
 template <int NETS>
 static const void *cta_kernel_ptr(int mem) {
     switch (mem) {
-    case kArrSmem: return (const void *)eat_cta_kernel<NETS, true, true>;
-    case kArrGlobalMaskSmem: return (const void *)eat_cta_kernel<NETS, false, true>;
+    case 0: return (const void *)eat_cta_kernel<NETS, true, true>;
+    case 1: return (const void *)eat_cta_kernel<NETS, false, true>;
     default: return (const void *)eat_cta_kernel<NETS, false, false>;
     }
 }
@@ -241,15 +324,9 @@ static cudaError_t launch_cta_t(const NetDev *nets, int n_nets, const QueryArgs 
     for (int i = 0; i < n_nets && i < NETS; ++i) tab.net[i] = nets[i];
     for (int i = n_nets; i < NETS; ++i) tab.net[i] = NetDev{};
     switch (mem) {
-    case kArrSmem:
-        eat_cta_kernel<NETS, true, true><<<grid, block, smem, st>>>(tab, qa);
-        break;
-    case kArrGlobalMaskSmem:
-        eat_cta_kernel<NETS, false, true><<<grid, block, smem, st>>>(tab, qa);
-        break;
-    default:
-        eat_cta_kernel<NETS, false, false><<<grid, block, smem, st>>>(tab, qa);
-        break;
+    case 0: eat_cta_kernel<NETS, true, true><<<grid, block, smem, st>>>(tab, qa); break;
+    case 1: eat_cta_kernel<NETS, false, true><<<grid, block, smem, st>>>(tab, qa); break;
+    default: eat_cta_kernel<NETS, false, false><<<grid, block, smem, st>>>(tab, qa); break;
     }
     return cudaGetLastError();
 }

@@ -13,17 +13,22 @@ struct QueryArgs {
     const int32_t *ts;         // [n]
     const int64_t *arr_off;    // [n] or nullptr (row q at q * n_stops)
     int32_t *arr_out;
-    int32_t *queues;           // [slots][queue_stride]
-    uint32_t *gmask;           // [slots][mask_stride] when the bitmap is global
+    int32_t *spill;            // [slots][spill_stride]: spilled frontier stops (2 x vmax)
+    uint32_t *gmask;           // [slots][mask_stride]: both bitmaps when not in shared memory
     int32_t *work;             // query counter (zeroed before launch)
     int32_t *status;           // [n] or nullptr
     eat_counters *counters;    // [n] or nullptr
-    int64_t queue_stride;      // ints per slot (>= 2 * max n_stops)
-    int64_t mask_stride;       // words per slot
+    int64_t spill_stride;      // ints per slot (>= 2 * vmax)
+    int64_t mask_stride;       // words per slot (>= 2 * mask_words) when global
     int32_t n;
     int32_t n_nets;
     int32_t max_rounds;
     int32_t vw_log2;           // lanes per active stop = 1 << vw_log2
+    int32_t vmax;              // largest n_stops in the launch
+    int32_t qcap;              // shared-memory (stop, type) items per buffer
+    int32_t mask_words;        // words per bitmap (padded)
+    int32_t smem_mask_off;     // int offset of the bitmaps in dynamic shared memory
+    int32_t smem_q_off;        // int offset of the item buffers in dynamic shared memory
 };
 
 // mem: 0 = arrivals and bitmap in shared memory, 1 = arrivals global / bitmap

@@ -47,12 +47,13 @@ class eat_stats(ctypes.Structure):
                 ("t0", ctypes.c_int32), ("max_clusters", ctypes.c_int32),
                 ("max_out_types", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("n_conn", ctypes.c_int64), ("n_ap", ctypes.c_int64),
-                ("n_cl", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("n_cl", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("k_min", ctypes.c_int32), ("y", ctypes.c_int32), ("n_ap_extra", ctypes.c_int64)]
 
 
 class eat_net_view(ctypes.Structure):
     _fields_ = [("row_ptr", _vp), ("type_rec", _vp), ("type_cl", _vp), ("cl", _vp),
-                ("ap", _vp)]
+                ("ap", _vp), ("type_dev", _vp), ("cluster_entries", _vp), ("ap_extra", _vp)]
 
 
 class eat_counters(ctypes.Structure):
@@ -216,6 +217,9 @@ def eat_net_host_view(net: Net) -> dict:
         "type_cl": arr(view.type_cl, T, np.int32),
         "cl": arr(view.cl, st["n_cl"], np.int32),
         "ap": arr(view.ap, 2 * st["n_ap"], np.uint32).reshape(-1, 2),
+        "type_dev": arr(view.type_dev, 4 * T, np.int32).reshape(T, 4),
+        "cluster_entries": arr(view.cluster_entries, 8 * T * st["y"], np.int32).reshape(T, st["y"], 8),
+        "ap_extra": arr(view.ap_extra, 2 * st["n_ap_extra"], np.uint32).reshape(-1, 2),
     }
 
 

@@ -141,3 +141,51 @@ def test_empty_timetable_and_host_only_queries():
     with pytest.raises(eat.EatError) as ei:
         eat.eat_query(net, 0, 0)
     assert ei.value.code == eat.EAT_ERR_NO_DEVICE
+
+
+@pytest.mark.parametrize("make,width,t0", [
+    (synth.small_grid, 0, 0),
+    (synth.small_grid, 900, 1000),
+    (lambda: synth.tiny_random(9, 400, 3, t_max=20000, dur_max=300), 3600, 0),
+    (lambda: synth.tiny_random(5, 300, 4, t_max=500, dur_max=5), 7, 0),
+    (lambda: synth.single_route(30000, 600, 40, [120, 60]), 1800, 0),
+])
+def test_device_cluster_entries_match_oracle(make, width, t0):
+    """Every (type, cluster) entry of the device layout holds exactly the oracle's greedy
+    cover of that cluster (first two APs inline, the rest in ap_extra, in order) and the
+    first departure of the next non-empty cluster (INF if none)."""
+    tt = make()
+    net = _build(tt, cluster_width=width, t0=t0)
+    hv, st = eat.eat_net_host_view(net), eat.eat_get_stats(net)
+    W = width or 3600
+    types = oracle.connection_types(tt)
+    rp, rec, tyd, ce, apx = (hv[k] for k in ("row_ptr", "type_rec", "type_dev",
+                                             "cluster_entries", "ap_extra"))
+    y, kmin = st["y"], st["k_min"]
+    all_k = [(d - t0) // W for ds in types.values() for d in ds]
+    assert kmin == min(all_k) and y == max(all_k) - kmin + 1
+
+    def dec(start, sc):
+        step, cnt = (sc >> 16) & 0xFFFF, sc & 0xFFFF
+        return (int(start), int(start) + (cnt - 1) * step, step)
+
+    for u in range(st["n_stops"]):
+        for t in range(rp[u], rp[u + 1]):
+            v, lam = int(rec[t][0]), int(rec[t][1])
+            assert tyd[t].tolist() == [v, lam, rp[v], rp[v + 1]]
+            deps = types[(u, v, lam)]
+            clusters = oracle.cluster_sets(deps, width=W, t0=t0)
+            for kr in range(y):
+                k = kmin + kr
+                e = ce[t, kr]
+                n = int(e[6])
+                got = []
+                if n >= 1:
+                    got.append(dec(e[0], int(e[1]) & 0xFFFFFFFF))
+                if n >= 2:
+                    got.append(dec(e[2], int(e[3]) & 0xFFFFFFFF))
+                for j in range(2, n):
+                    got.append(dec(apx[e[5] + j - 2][0], int(apx[e[5] + j - 2][1])))
+                assert got == ap_cover(clusters.get(k, []))
+                later = [d for d in deps if (d - t0) // W > k]
+                assert int(e[4]) == (min(later) if later else INF)
