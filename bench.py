@@ -80,6 +80,7 @@ def describe(name, tt, batch):
                  "stops, headway 3-30 min, 10% jittered trips, 3 duration bands",
     }[name]
     return {"workload": desc, "global_batch": batch, "n_stops": int(tt.n_stops),
+            "method": "Cluster-AP fixpoint (one thread block per query)",
             "n_connections": int(tt.n_conn), "times": "int32 seconds",
             "l2": "flushed before every step (256 MB write)", "parallelism": "replicas"}
 
@@ -234,7 +235,10 @@ def run_ours(args):
     from paper_1912_00966_gb300 import eat
 
     tt, batch = workload(args.workload)
-    net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=dev)
+    t_build = time.perf_counter()
+    net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=dev, trip=tt.trip,
+                        subtrips=args.subtrips)
+    t_build = time.perf_counter() - t_build
     st = eat.eat_get_stats(net)
     V = tt.n_stops
     n_steps = args.warmup + args.steps
@@ -303,6 +307,24 @@ def run_ours(args):
         eat.eat_query_batch(net, src_h[i], ts_h[i], out_h, stream=stream, **opts)
         e2e_t.append(time.perf_counter() - t0)
 
+    # The same steps on the network without sub-trips (Section III-G off), for comparison.
+    base_ms = None
+    if args.subtrips:
+        net0 = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=dev)
+        ws0 = torch.empty(eat.eat_workspace_bytes(net0, batch, **opts), dtype=torch.uint8,
+                          device="cuda")
+        e0 = []
+        for i in range(min(n_steps, args.warmup + 50)):
+            flush.fill_(i)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            eat.eat_query_batch(net0, src_d[i], ts_d[i], out, workspace=ws0, stream=stream, **opts)
+            b.record(stream)
+            e0.append((a, b))
+        torch.cuda.synchronize()
+        base_ms = statistics.mean(a.elapsed_time(b) for a, b in e0[args.warmup:])
+        net0.close()
+
     # Plain single-query fixpoint (one blocking query at a time), for comparison.
     plain_n = min(64, batch)
     row = torch.empty(V, dtype=torch.int32, device="cuda")
@@ -357,11 +379,15 @@ def run_ours(args):
                      "kernel": "eat_cta_kernel", "alg_bytes_per_launch": per_launch},
         "cpu_baseline": cpu,
         "connections_relaxed_per_s": tot["types"] / (gpu_s / world),
+        "subtrips": {0: "none", 1: "sqrt(k) per trip", 2: "sqrt(mean trip length)"}[args.subtrips],
+        "without_subtrips": None if base_ms is None else
+            {"value": batch / (base_ms / 1e3), "unit": "queries/s", "ms_per_step": base_ms},
+        "build_s": t_build,
         "plain_single_query": {"value": plain_n / plain_s, "unit": "queries/s",
                                "ms_per_query": 1e3 * plain_s / plain_n},
         "work_per_query": {n: tot[n] / (batch * args.steps) for n in names},
         "network": {k: st[k] for k in ("n_types", "n_edges", "n_ap", "n_cl", "max_clusters",
-                                       "device_bytes")},
+                                       "device_bytes", "n_shortcuts", "y")},
         "clocks": clocks.summary(),
         "kernel_hash": h,
         "wall_s_timed_region": t_wall,
@@ -380,6 +406,8 @@ def main():
     ap.add_argument("--vwarp", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--subtrips", type=int, default=1, choices=[0, 1, 2],
+                    help="sub-trip shortcuts (Section III-G): 0 none, 1 sqrt(k), 2 sqrt(mean)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

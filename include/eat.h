@@ -58,7 +58,11 @@ typedef struct eat_net eat_net;
 /* Input timetable: n_conn connections as four parallel int32 arrays in host
  * memory (Section II, Preliminaries).  Requirements, checked by eat_build:
  * 0 <= u, v < n_stops; dur >= 1; dep >= t0 (see eat_build_opts);
- * dep + dur < INT32_MAX.  Identical connections are merged. */
+ * dep + dur < INT32_MAX.  Identical connections are merged.
+ * `trip` (nullable) gives each connection's trip (vehicle run, Section III-G);
+ * connections with a negative trip id belong to no trip.  The connections of a
+ * trip, ordered by departure, must form a time-respecting chain (each one leaves
+ * the stop the previous one reached, no earlier than it arrived). */
 typedef struct {
     int32_t n_stops;
     int64_t n_conn;
@@ -66,14 +70,22 @@ typedef struct {
     const int32_t *v;
     const int32_t *dep;
     const int32_t *dur;
+    const int32_t *trip;
 } eat_connections;
+
+/* Sub-trip data enhancement (Section III-G). */
+enum eat_subtrips {
+    EAT_SUBTRIPS_NONE = 0,
+    EAT_SUBTRIPS_SQRT_K = 1,     /* trip of k connections: sub-trips of round(sqrt(k)) */
+    EAT_SUBTRIPS_SQRT_MEAN = 2   /* every trip: sub-trips of round(sqrt(mean trip length)) */
+};
 
 /* Build options.  Zero-initialise for the paper's defaults. */
 typedef struct {
     int32_t cluster_width; /* seconds per cluster, 1..65535; 0 = 3600 (Section III-D) */
     int32_t t0;            /* start of cluster 0; departures must be >= t0; default 0 */
     int32_t device;        /* CUDA device ordinal; -1 = host-only build (inspection only) */
-    int32_t reserved;
+    int32_t subtrips;      /* EAT_SUBTRIPS_*; needs conn->trip */
 } eat_build_opts;
 
 /* Sizes of a built network. */
@@ -93,6 +105,7 @@ typedef struct {
     int32_t k_min;          /* device layout: first cluster index stored */
     int32_t y;              /* device layout: clusters stored per type (the paper's y) */
     int64_t n_ap_extra;     /* device layout: APs beyond the two kept in a cluster entry */
+    int64_t n_shortcuts;    /* artificial sub-trip connections added (Section III-G) */
 } eat_stats;
 
 /* Read-only host view of the built arrays (Section IV-A's CT[], CL[], AP[], in
@@ -181,11 +194,15 @@ int32_t eat_version(void);
  * edge and duration into connection types (Section III-B), split each type by
  * departure time into clusters of cluster_width seconds (Section III-D), cover
  * each cluster by the greedy AP cover (Section II; Section III-C), order the
- * APs of a cluster by first term.
+ * APs of a cluster by first term.  With opts->subtrips, each trip is first cut
+ * into consecutive sub-trips and one artificial connection is added per
+ * sub-trip of two or more connections, from its first stop at its first
+ * departure to its last stop at its last arrival (Section III-G); earliest
+ * arrival times are unchanged.
  *   conn  host arrays, read only during the call (copied).
  *   opts  may be NULL (defaults).
  *   out   receives a new network owned by the caller; release with eat_free.
- * Errors: EAT_ERR_INVALID (bad sizes, ids, durations, times or options),
+ * Errors: EAT_ERR_INVALID (bad sizes, ids, durations, times, trips or options),
  * EAT_ERR_OOM, EAT_ERR_CUDA, EAT_ERR_NO_DEVICE.  On error *out is NULL.
  */
 int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net **out);

@@ -280,7 +280,25 @@ int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net *
     const int32_t width = o.cluster_width ? o.cluster_width : 3600;
     eat_net *net = new (std::nothrow) eat_net();
     if (!net) return fail(EAT_ERR_OOM, "host allocation failed");
-    int rc = build_host(conn, width, o.t0, net->host);
+    int rc = EAT_OK;
+    if (o.subtrips != EAT_SUBTRIPS_NONE) {
+        // Check the plain input first so that errors name the caller's connections.
+        eat_connections plain = *conn;
+        plain.trip = nullptr;
+        eat::HostNet scratch;
+        rc = build_host(&plain, width, o.t0, scratch);
+        std::vector<int32_t> u, v, dep, dur;
+        int64_t added = 0;
+        if (!rc) rc = add_subtrips(conn, o.subtrips, u, v, dep, dur, added);
+        if (!rc) {
+            eat_connections aug{conn->n_stops, (int64_t)u.size(), u.data(), v.data(), dep.data(),
+                                dur.data(), nullptr};
+            rc = build_host(&aug, width, o.t0, net->host);
+            net->host.n_shortcuts = added;
+        }
+    } else {
+        rc = build_host(conn, width, o.t0, net->host);
+    }
     if (!rc) rc = build_fused(net->host);
     if (rc) {
         delete net;
@@ -375,6 +393,7 @@ int eat_get_stats(const eat_net *net, eat_stats *out) {
     out->k_min = h.k_min;
     out->y = h.y;
     out->n_ap_extra = (int64_t)h.apx.size() / 2;
+    out->n_shortcuts = h.n_shortcuts;
     return EAT_OK;
 }
 

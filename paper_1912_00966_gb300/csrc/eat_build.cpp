@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <thread>
 
@@ -274,6 +275,93 @@ int build_host(const eat_connections *c, int32_t width, int32_t t0, HostNet &h) 
         }
     }
     h.row_ptr[V] = r;
+    return EAT_OK;
+}
+
+// Sub-trips (Section III-G).  A trip of k connections, ordered by departure, is cut
+// into consecutive sub-trips of r connections (the last one shorter); r is the
+// nearest integer to sqrt(k) (EAT_SUBTRIPS_SQRT_K) or to the square root of the
+// mean trip length (EAT_SUBTRIPS_SQRT_MEAN), at least 2.  A sub-trip
+// (v_i, v_i+1, t_i, l_i) ... (v_j, v_j+1, t_j, l_j) with i < j yields one artificial
+// connection (v_i, v_j+1, t_i, t_j + l_j - t_i): riding the same vehicle, so no
+// earliest arrival changes, but a path needs fewer connections.
+int add_subtrips(const eat_connections *c, int32_t scheme, std::vector<int32_t> &u,
+                 std::vector<int32_t> &v, std::vector<int32_t> &dep, std::vector<int32_t> &dur,
+                 int64_t &n_added) {
+    n_added = 0;
+    const int64_t C = c->n_conn;
+    if (scheme != EAT_SUBTRIPS_SQRT_K && scheme != EAT_SUBTRIPS_SQRT_MEAN)
+        return fail(EAT_ERR_INVALID, "subtrips must be one of EAT_SUBTRIPS_*");
+    if (C > 0 && !c->trip) return fail(EAT_ERR_INVALID, "sub-trips need trip ids (conn->trip)");
+    // Group connection indices by trip (counting sort when ids are dense), then by departure.
+    int32_t max_trip = -1;
+    for (int64_t i = 0; i < C; ++i) max_trip = std::max(max_trip, c->trip[i]);
+    std::vector<int64_t> idx;
+    std::vector<int64_t> start;
+    if (max_trip >= 0 && (int64_t)max_trip <= 4 * C + 1024) {
+        std::vector<int64_t> cnt((size_t)max_trip + 2, 0);
+        for (int64_t i = 0; i < C; ++i)
+            if (c->trip[i] >= 0) ++cnt[(size_t)c->trip[i] + 1];
+        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+        idx.resize((size_t)cnt.back());
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t i = 0; i < C; ++i)
+            if (c->trip[i] >= 0) idx[(size_t)pos[(size_t)c->trip[i]]++] = i;
+        start.assign(cnt.begin(), cnt.end());
+    } else if (max_trip >= 0) {
+        for (int64_t i = 0; i < C; ++i)
+            if (c->trip[i] >= 0) idx.push_back(i);
+        std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+            return c->trip[a] < c->trip[b] || (c->trip[a] == c->trip[b] && a < b);
+        });
+        start.push_back(0);
+        for (size_t k = 1; k <= idx.size(); ++k)
+            if (k == idx.size() || c->trip[idx[k]] != c->trip[idx[k - 1]]) start.push_back((int64_t)k);
+    } else {
+        start.push_back(0);
+    }
+    const size_t n_groups = start.size() - 1;
+    int64_t sum_k = 0, n_trips = 0;
+    for (size_t g = 0; g < n_groups; ++g) {
+        int64_t *b = idx.data() + start[g], *e = idx.data() + start[g + 1];
+        if (b == e) continue;
+        std::sort(b, e, [&](int64_t x, int64_t y) { return c->dep[x] < c->dep[y]; });
+        for (int64_t *p = b + 1; p < e; ++p) {
+            const int64_t a = p[-1], z = p[0];
+            if (c->v[a] != c->u[z] || (int64_t)c->dep[a] + c->dur[a] > (int64_t)c->dep[z])
+                return fail(EAT_ERR_INVALID, "trip " + std::to_string(c->trip[z]) +
+                                                 " is not a time-respecting chain of connections");
+        }
+        sum_k += e - b;
+        ++n_trips;
+    }
+    const int64_t r_mean = n_trips ? std::max<int64_t>(2, (int64_t)std::llround(std::sqrt((double)sum_k / (double)n_trips))) : 2;
+    try {
+        u.assign(c->u, c->u + C);
+        v.assign(c->v, c->v + C);
+        dep.assign(c->dep, c->dep + C);
+        dur.assign(c->dur, c->dur + C);
+        for (size_t g = 0; g < n_groups; ++g) {
+            const int64_t *b = idx.data() + start[g];
+            const int64_t k = start[g + 1] - start[g];
+            if (k < 2) continue;
+            const int64_t r = scheme == EAT_SUBTRIPS_SQRT_K
+                                  ? std::max<int64_t>(2, (int64_t)std::llround(std::sqrt((double)k)))
+                                  : r_mean;
+            for (int64_t i = 0; i < k; i += r) {
+                const int64_t j = std::min(i + r, k) - 1;
+                if (j <= i) continue;
+                const int64_t first = b[i], last = b[j];
+                u.push_back(c->u[first]);
+                v.push_back(c->v[last]);
+                dep.push_back(c->dep[first]);
+                dur.push_back((int32_t)((int64_t)c->dep[last] + c->dur[last] - c->dep[first]));
+                ++n_added;
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        return fail(EAT_ERR_OOM, "host allocation for sub-trips failed");
+    }
     return EAT_OK;
 }
 

@@ -52,6 +52,7 @@ struct HostNet {
     int32_t n_stops = 0, n_types = 0, n_edges = 0, width = 3600, t0 = 0;
     int32_t max_clusters = 0, max_out_types = 0;
     int64_t n_conn = 0;
+    int64_t n_shortcuts = 0;
     std::vector<int32_t> row_ptr;    // V + 1
     std::vector<int32_t> type_rec;   // 4 T
     std::vector<int32_t> type_cl;    // T
@@ -88,6 +89,12 @@ void clear_error();
 
 // Host preprocessing (eat_build.cpp): fills `h` from the connections.
 int build_host(const eat_connections *c, int32_t width, int32_t t0, HostNet &h);
+
+// Sub-trips (eat_build.cpp): the connections plus one artificial connection per
+// sub-trip of >= 2 connections (Section III-G), as new SoA arrays.
+int add_subtrips(const eat_connections *c, int32_t scheme, std::vector<int32_t> &u,
+                 std::vector<int32_t> &v, std::vector<int32_t> &dep, std::vector<int32_t> &dur,
+                 int64_t &n_added);
 
 // Device layout from the logical arrays (eat_build.cpp).
 int build_fused(HostNet &h);

@@ -20,6 +20,7 @@ EAT_OK, EAT_ERR_INVALID, EAT_ERR_OOM, EAT_ERR_CUDA = 0, 1, 2, 3
 EAT_ERR_NO_CONVERGENCE, EAT_ERR_NO_DEVICE, EAT_ERR_WORKSPACE = 4, 5, 6
 EAT_MODE_AUTO, EAT_MODE_CTA, EAT_MODE_GRID = 0, 1, 2
 EAT_PLACE_AUTO, EAT_PLACE_SHARED, EAT_PLACE_GLOBAL_ARR, EAT_PLACE_GLOBAL = 0, 1, 2, 3
+EAT_SUBTRIPS_NONE, EAT_SUBTRIPS_SQRT_K, EAT_SUBTRIPS_SQRT_MEAN = 0, 1, 2
 EAT_MAX_NETS = 128
 
 if not os.path.exists(LIB_PATH):
@@ -33,12 +34,12 @@ _vp = ctypes.c_void_p
 
 class eat_connections(ctypes.Structure):
     _fields_ = [("n_stops", ctypes.c_int32), ("n_conn", ctypes.c_int64),
-                ("u", _vp), ("v", _vp), ("dep", _vp), ("dur", _vp)]
+                ("u", _vp), ("v", _vp), ("dep", _vp), ("dur", _vp), ("trip", _vp)]
 
 
 class eat_build_opts(ctypes.Structure):
     _fields_ = [("cluster_width", ctypes.c_int32), ("t0", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("subtrips", ctypes.c_int32)]
 
 
 class eat_stats(ctypes.Structure):
@@ -48,7 +49,8 @@ class eat_stats(ctypes.Structure):
                 ("max_out_types", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("n_conn", ctypes.c_int64), ("n_ap", ctypes.c_int64),
                 ("n_cl", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("k_min", ctypes.c_int32), ("y", ctypes.c_int32), ("n_ap_extra", ctypes.c_int64)]
+                ("k_min", ctypes.c_int32), ("y", ctypes.c_int32), ("n_ap_extra", ctypes.c_int64),
+                ("n_shortcuts", ctypes.c_int64)]
 
 
 class eat_net_view(ctypes.Structure):
@@ -174,15 +176,19 @@ class Net:
         return eat_get_stats(self)
 
 
-def eat_build(n_stops, u, v, dep, dur, cluster_width=0, t0=0, device=0) -> Net:
+def eat_build(n_stops, u, v, dep, dur, cluster_width=0, t0=0, device=0, trip=None,
+              subtrips=EAT_SUBTRIPS_NONE) -> Net:
     """Preprocess connections (host int32 arrays) into a device-resident network."""
     u, v, dep, dur = _i32(u), _i32(v), _i32(dep), _i32(dur)
     n = u.shape[0]
     if not (v.shape[0] == dep.shape[0] == dur.shape[0] == n):
         raise ValueError("connection arrays differ in length")
+    tr = None if trip is None else _i32(trip)
+    if tr is not None and tr.shape[0] != n:
+        raise ValueError("trip array differs in length")
     c = eat_connections(int(n_stops), int(n), u.ctypes.data, v.ctypes.data, dep.ctypes.data,
-                        dur.ctypes.data)
-    o = eat_build_opts(int(cluster_width), int(t0), int(device), 0)
+                        dur.ctypes.data, None if tr is None else tr.ctypes.data)
+    o = eat_build_opts(int(cluster_width), int(t0), int(device), int(subtrips))
     h = _vp()
     _check(_lib.eat_build(ctypes.byref(c), ctypes.byref(o), ctypes.byref(h)), "eat_build")
     return Net(h.value)

@@ -189,3 +189,85 @@ def test_device_cluster_entries_match_oracle(make, width, t0):
                 assert got == ap_cover(clusters.get(k, []))
                 later = [d for d in deps if (d - t0) // W > k]
                 assert int(e[4]) == (min(later) if later else INF)
+
+
+# ------------------------------------------------------------------ sub-trips (Section III-G)
+
+def _expand_connections(net):
+    """All connections (u, v, t, lambda) encoded by a built network, from its host view."""
+    hv, st = eat.eat_net_host_view(net), eat.eat_get_stats(net)
+    rp, rec, clb, cl, ap = hv["row_ptr"], hv["type_rec"], hv["type_cl"], hv["cl"], hv["ap"]
+    W, t0 = st["cluster_width"], st["t0"]
+    out = []
+    for u in range(st["n_stops"]):
+        for t in range(rp[u], rp[u + 1]):
+            v, lam, first, last = (int(x) for x in rec[t])
+            for a in range(cl[clb[t] + (first - t0) // W], cl[clb[t] + (last - t0) // W + 1]):
+                start, packed = int(ap[a, 0]), int(ap[a, 1])
+                step, cnt = packed >> 16, packed & 0xFFFF
+                for m in range(cnt):
+                    out.append((u, v, start + m * step, lam))
+    return sorted(set(out))
+
+
+def test_subtrips_on_one_route():
+    # 9 connections per trip (stops 0..9): sqrt(9) = 3, so sub-trips 0-3, 3-6, 6-9.
+    durs = [100, 200, 300, 50, 60, 70, 400, 10, 20]
+    tt = synth.single_route(30000, 600, 5, durs)
+    net = _build(tt, trip=tt.trip, subtrips=eat.EAT_SUBTRIPS_SQRT_K)
+    st = eat.eat_get_stats(net)
+    assert st["n_shortcuts"] == 3 * 5
+    got = _expand_connections(net)
+    cum = np.concatenate([[0], np.cumsum(durs)])
+    for j in range(5):
+        for a, b in ((0, 3), (3, 6), (6, 9)):
+            assert (a, b, 30000 + 600 * j + int(cum[a]), int(cum[b] - cum[a])) in got
+    assert len(got) == tt.n_conn + 15
+
+
+def test_subtrips_mean_length_scheme():
+    # Trips of 4 and 16 connections: mean 10, so sub-trips of round(sqrt(10)) = 3 everywhere.
+    a = synth.single_route(1000, 1000, 1, [10] * 4, stops=np.arange(5))
+    b = synth.single_route(2000, 1000, 1, [10] * 16, stops=np.arange(10, 27))
+    cat = lambda f: np.concatenate([getattr(a, f), getattr(b, f)])
+    trip = np.concatenate([a.trip, b.trip + 1])
+    tt = synth.Timetable("two", 27, cat("u"), cat("v"), cat("dep"), cat("dur"), trip, cat("seq"))
+    per_k = eat.eat_get_stats(_build(tt, trip=trip, subtrips=eat.EAT_SUBTRIPS_SQRT_K))
+    mean = eat.eat_get_stats(_build(tt, trip=trip, subtrips=eat.EAT_SUBTRIPS_SQRT_MEAN))
+    # sqrt(k): r = 2 for 4 (2 shortcuts), r = 4 for 16 (4 shortcuts); mean: r = 3 -> 1 + 5.
+    assert per_k["n_shortcuts"] == 6
+    assert mean["n_shortcuts"] == 6
+    got = _expand_connections(_build(tt, trip=trip, subtrips=eat.EAT_SUBTRIPS_SQRT_MEAN))
+    assert (0, 3, 1000, 30) in got and (3, 4, 1030, 10) in got and (10, 13, 2000, 30) in got
+
+
+def test_subtrips_reject_broken_trips_and_missing_ids():
+    tt = synth.small_grid()
+    bad = tt.trip.copy()
+    bad[5], bad[500] = bad[500], bad[5]            # two connections swap trips
+    with pytest.raises(eat.EatError) as ei:
+        _build(tt, trip=bad, subtrips=eat.EAT_SUBTRIPS_SQRT_K)
+    assert ei.value.code == eat.EAT_ERR_INVALID and "trip" in str(ei.value)
+    with pytest.raises(eat.EatError) as ei:
+        _build(tt, subtrips=eat.EAT_SUBTRIPS_SQRT_K)
+    assert ei.value.code == eat.EAT_ERR_INVALID
+    with pytest.raises(eat.EatError):
+        _build(tt, trip=tt.trip, subtrips=7)
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_subtrips_leave_earliest_arrivals_unchanged(scheme):
+    """Section III-G: the artificial connections ride the same vehicle, so the earliest
+    arrival times of the enhanced timetable equal the original's (oracle on both)."""
+    tt = synth.small_grid()
+    net = _build(tt, trip=tt.trip, subtrips=scheme)
+    conns = np.array(_expand_connections(net), dtype=np.int64)
+    z = np.zeros(len(conns), np.int32)
+    enh = synth.Timetable("enh", tt.n_stops, conns[:, 0].astype(np.int32), conns[:, 1].astype(np.int32),
+                          conns[:, 2].astype(np.int32), conns[:, 3].astype(np.int32), z, z)
+    assert len(conns) > tt.n_conn
+    a, b = oracle.SortedConnections(tt), oracle.SortedConnections(enh)
+    q = synth.random_queries(tt, 40, scheme)
+    ra, _ = oracle.csa_many(a, q.source, q.t_s, 4)
+    rb, _ = oracle.csa_many(b, q.source, q.t_s, 4)
+    assert np.array_equal(ra, rb)

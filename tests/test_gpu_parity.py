@@ -31,6 +31,8 @@ def _dev(a):
 class Case:
     def __init__(self, eat, tt, **kw):
         self.tt = tt
+        if kw.get("subtrips"):
+            kw.setdefault("trip", tt.trip)
         self.net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=0, **kw)
         self.sc = oracle.SortedConnections(tt)
         self.V = tt.n_stops
@@ -289,3 +291,27 @@ def test_large_network_sampled(eat):
     assert np.array_equal(got[idx], want)
     for i in np.random.default_rng(1).choice(1024, 4, replace=False):
         assert oracle.certify(tt, int(q.source[i]), int(q.t_s[i]), got[i]) == (0, -1)
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_subtrips_same_arrivals_fewer_rounds(eat, city, scheme):
+    """Section III-G: with sub-trip shortcuts the arrivals equal the oracle's on the original
+    timetable, and queries need fewer rounds."""
+    enh = Case(eat, city.tt, subtrips=scheme)
+    q = synth.random_queries(city.tt, 256, 0x5B + scheme)
+    got, status, cnt = enh.run(eat, q.source, q.t_s)
+    assert (status == 0).all()
+    assert np.array_equal(got, city.oracle_rows(q.source, q.t_s))
+    _, _, base = city.run(eat, q.source, q.t_s)
+    assert cnt[:, 0].mean() < 0.8 * base[:, 0].mean()
+    assert cnt[:, 0].max() < base[:, 0].max()
+
+
+def test_subtrips_small_grid_all_queries(eat, small):
+    enh = Case(eat, small.tt, subtrips=1)
+    q = synth.random_queries(small.tt, 300, 77)
+    got, status, _ = enh.run(eat, q.source, q.t_s)
+    assert (status == 0).all()
+    assert np.array_equal(got, small.oracle_rows(q.source, q.t_s))
+    for s_, t_ in [(0, 28800), (0, 0), (5, 86000)]:
+        assert np.array_equal(eat.eat_query(enh.net, s_, t_), oracle.csa(small.sc, s_, t_))
