@@ -237,7 +237,7 @@ def run_ours(args):
     tt, batch = workload(args.workload)
     t_build = time.perf_counter()
     net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=dev, trip=tt.trip,
-                        subtrips=args.subtrips)
+                        subtrips=args.subtrips, cluster_width=args.cluster_width)
     t_build = time.perf_counter() - t_build
     st = eat.eat_get_stats(net)
     V = tt.n_stops
@@ -310,7 +310,8 @@ def run_ours(args):
     # The same steps on the network without sub-trips (Section III-G off), for comparison.
     base_ms = None
     if args.subtrips:
-        net0 = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=dev)
+        net0 = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=dev,
+                             cluster_width=args.cluster_width)
         ws0 = torch.empty(eat.eat_workspace_bytes(net0, batch, **opts), dtype=torch.uint8,
                           device="cuda")
         e0 = []
@@ -380,6 +381,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "connections_relaxed_per_s": tot["types"] / (gpu_s / world),
         "subtrips": {0: "none", 1: "sqrt(k) per trip", 2: "sqrt(mean trip length)"}[args.subtrips],
+        "cluster_width_s": args.cluster_width,
         "without_subtrips": None if base_ms is None else
             {"value": batch / (base_ms / 1e3), "unit": "queries/s", "ms_per_step": base_ms},
         "build_s": t_build,
@@ -406,7 +408,9 @@ def main():
     ap.add_argument("--vwarp", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=10.0)
-    ap.add_argument("--subtrips", type=int, default=1, choices=[0, 1, 2],
+    ap.add_argument("--cluster-width", type=int, default=1800,
+                    help="seconds per departure cluster (Section III-D uses one hour; Section V-B finds narrower clusters faster)")
+    ap.add_argument("--subtrips", type=int, default=0, choices=[0, 1, 2],
                     help="sub-trip shortcuts (Section III-G): 0 none, 1 sqrt(k), 2 sqrt(mean)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -356,6 +356,7 @@ int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net *
         d.n_types = h.n_types;
         d.t0 = h.t0;
         d.width = h.width;
+        d.inv_width = 1.0f / (float)h.width;
         d.k_min = h.k_min;
         d.y = h.y;
     }

@@ -389,8 +389,11 @@ int build_fused(HostNet &h) {
         const int32_t kf = (h.type_rec[4 * (size_t)t + 2] - t0) / W;
         const int32_t kl = (h.type_rec[4 * (size_t)t + 3] - t0) / W;
         const int32_t b = h.type_cl[t];
-        int64_t extra = 0;
-        for (int32_t k = kf; k <= kl; ++k) extra += std::max(0, h.cl[b + k + 1] - h.cl[b + k] - 2);
+        int64_t extra = 0;   // each cluster's list padded to an even length (16-byte aligned)
+        for (int32_t k = kf; k <= kl; ++k) {
+            const int32_t m = std::max(0, h.cl[b + k + 1] - h.cl[b + k] - 2);
+            extra += m + (m & 1);
+        }
         xoff[t + 1] = xoff[t] + extra;
     }
     if (xoff[T] >= INT32_MAX) return fail(EAT_ERR_INVALID, "too many APs for 32-bit indices");
@@ -431,6 +434,11 @@ int build_fused(HostNet &h) {
                 for (int32_t j = 2; j < n; ++j, ++x) {
                     h.apx[2 * (size_t)x] = h.ap[2 * (size_t)(lo + j)];
                     h.apx[2 * (size_t)x + 1] = h.ap[2 * (size_t)(lo + j) + 1];
+                }
+                if (n > 2 && ((n - 2) & 1)) {     // padding entry, never examined
+                    h.apx[2 * (size_t)x] = (uint32_t)EAT_INF;
+                    h.apx[2 * (size_t)x + 1] = 0u;
+                    ++x;
                 }
             }
             int32_t next = EAT_INF;

@@ -37,6 +37,7 @@ struct NetDev {
     int32_t n_types;
     int32_t t0;
     int32_t width;            // cluster width (seconds)
+    float inv_width;          // 1 / width, for the cluster index of times < 2^22 s
     int32_t k_min;            // first cluster index stored
     int32_t y;                // clusters stored per type
 };

@@ -38,13 +38,27 @@ namespace eat {
 
 constexpr int32_t kInf = INT32_MAX;
 
+// ceil(a / b) for 1 <= a, b < 2^16 without an integer divide: a fast float
+// quotient (a few ulp of error, i.e. well under 1 for quotients < 2^16) rounded
+// down, then made exact with the integer remainder.
+__device__ __forceinline__ int32_t ceil_div_small(int32_t a, int32_t b) {
+    int32_t q = __float2int_rz(__fdividef((float)a, (float)b));
+    int32_t r = a - q * b;
+    if (r < 0) { --q; r += b; }
+    else if (r >= b) { ++q; r -= b; }
+    return q + (r > 0);
+}
+
 // Least term >= e of the AP {start, sc = difference << 16 | terms}, or kInf.
+// Only a many-term AP that straddles e needs arithmetic (Algorithm 6's
+// ceil((e - start) / difference)); e - start < cluster width < 2^16 there.
 __device__ __forceinline__ int32_t ap_candidate(int32_t start, uint32_t sc, int32_t e) {
     if (e <= start) return start;
+    const int32_t cnt = (int32_t)(sc & 0xffffu);
+    if (cnt <= 1) return kInf;
     const int32_t step = (int32_t)(sc >> 16);
-    const int32_t last = start + ((int32_t)(sc & 0xffffu) - 1) * step;
-    if (e > last) return kInf;                 // also every one-term AP
-    return start + ((e - start + step - 1) / step) * step;
+    if (e > start + (cnt - 1) * step) return kInf;
+    return start + ceil_div_small(e - start, step) * step;
 }
 
 // getConnectionFromAPs (Algorithm 6) over the APs of one cluster entry, with the
@@ -61,11 +75,22 @@ __device__ __forceinline__ int32_t cluster_lookup(const int4 c0, const int4 c1, 
         if (n > 1 && c0.z < tc) {             // APs are ordered by first term
             ++aps;
             tc = min(tc, ap_candidate(c0.z, (uint32_t)c0.w, e));
-            for (int32_t j = 2; j < n; ++j) {
-                const uint2 r = __ldg(apx + c1.y + (j - 2));
-                if ((int32_t)r.x >= tc) break;
-                ++aps;
-                tc = min(tc, ap_candidate((int32_t)r.x, r.y, e));
+            // Further APs: batches of 8 loaded together (the list is 16-byte aligned
+            // and padded to an even length), so one L2 round trip covers a batch.
+            const int32_t m = n - 2;
+            const uint4 *p = reinterpret_cast<const uint4 *>(apx + c1.y);
+            for (int32_t j = 0; j < m; j += 8) {
+                uint4 r[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    r[q] = (j + 2 * q < m) ? __ldg(p + (j >> 1) + q) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (j + 2 * q < m) tc = min(tc, ap_candidate((int32_t)r[q].x, r[q].y, e));
+                    if (j + 2 * q + 1 < m) tc = min(tc, ap_candidate((int32_t)r[q].z, r[q].w, e));
+                }
+                aps += min(8, m - j);
+                if (j + 8 < m && (int32_t)r[3].z >= tc) break;   // later starts are larger
             }
         }
     }
@@ -77,7 +102,18 @@ __device__ __forceinline__ int32_t cluster_lookup(const int4 c0, const int4 c1, 
 // no departure at or after e exists in the network.
 __device__ __forceinline__ int32_t cluster_slot(const NetDev &N, int32_t e) {
     const int64_t d = (int64_t)e - N.t0;
-    const int32_t k = d < 0 ? 0 : (int32_t)((uint32_t)d / (uint32_t)N.width) - N.k_min;
+    if (d < 0) return 0;
+    int32_t q;
+    if (d < (1 << 22)) {       // float quotient, exact after one remainder step
+        const int32_t di = (int32_t)d;
+        q = __float2int_rz((float)di * N.inv_width);
+        const int32_t r = di - q * N.width;
+        if (r < 0) --q;
+        else if (r >= N.width) ++q;
+    } else {
+        q = (int32_t)((uint32_t)d / (uint32_t)N.width);
+    }
+    const int32_t k = q - N.k_min;
     return k < 0 ? 0 : k;
 }
 
