@@ -61,6 +61,170 @@ def kernel_hash() -> str:
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
+RAGGED_QUERIES = 4096
+
+
+def run_ours_ragged(args):
+    """64 grid networks of 1k-50k stops, 4,096 queries per step in one launch."""
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    from paper_1912_00966_gb300 import eat
+
+    tts = synth.ragged_grids(64)
+    t_build = time.perf_counter()
+    nets = [eat.eat_build(t.n_stops, t.u, t.v, t.dep, t.dur, device=dev,
+                          cluster_width=args.cluster_width) for t in tts]
+    t_build = time.perf_counter() - t_build
+    n_steps = args.warmup + args.steps
+    Q = RAGGED_QUERIES
+    qsets = [synth.random_queries(tts, Q, 0xA0 + 1000 * rank + i) for i in range(n_steps)]
+    Vs = np.array([t.n_stops for t in tts], np.int64)
+    offs = [np.concatenate([[0], np.cumsum(Vs[q.net])[:-1]]).astype(np.int64) for q in qsets]
+    total = max(int(Vs[q.net].sum()) for q in qsets)
+    dq = [(torch.as_tensor(q.net).cuda(), torch.as_tensor(q.source).cuda(),
+           torch.as_tensor(q.t_s).cuda(), torch.as_tensor(o).cuda()) for q, o in zip(qsets, offs)]
+    out = torch.empty(total, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros((n_steps, Q, 7), dtype=torch.int64, device="cuda")
+    status = torch.zeros((n_steps, Q), dtype=torch.int32, device="cuda")
+    opts = dict(vwarp=args.vwarp, block=args.block)
+    ws = torch.empty(eat.eat_workspace_bytes(nets, Q, **opts), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n_steps)]
+
+    def step(i):
+        flush.fill_(i)
+        a, b = evs[i]
+        a.record(stream)
+        ni, src, ts, of = dq[i]
+        eat.eat_query_batch_multi(nets, ni, src, ts, out, of, workspace=ws, stream=stream,
+                                  status=status[i], counters=cnt[i], **opts)
+        b.record(stream)
+
+    with ClockSampler(dev) as clocks:
+        clocks.wait_first()
+        for i in range(args.warmup):
+            step(i)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.mark()
+        for i in range(args.warmup, n_steps):
+            step(i)
+        torch.cuda.synchronize()
+        time.sleep(0.06)
+        clocks.stop_mark()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(args.warmup, n_steps)]
+    gpu_s = sum(step_ms) / 1e3
+    if (status.cpu().numpy() != 0).any():
+        raise SystemExit("bench: a query did not converge")
+    c = cnt[args.warmup:].sum(dim=(0, 1)).cpu().numpy()
+    names = eat.COUNTER_FIELDS
+    tot = {n: int(c[k]) for k, n in enumerate(names)}
+    alg_bytes = sum(BYTES[n] * tot[n] for n in BYTES) + sum(
+        8 * int(Vs[q.net].sum()) for q in qsets[args.warmup:])
+    per_launch = alg_bytes / args.steps
+    mean_ms = gpu_s * 1e3 / args.steps
+
+    # End to end through the C ABI from pinned host buffers (rows copied back).
+    hq = [(torch.as_tensor(q.net).pin_memory(), torch.as_tensor(q.source).pin_memory(),
+           torch.as_tensor(q.t_s).pin_memory(), torch.as_tensor(o).pin_memory())
+          for q, o in zip(qsets, offs)]
+    out_h = torch.empty(total, dtype=torch.int32).pin_memory()
+    e2e_t = []
+    for i in range(n_steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eat.eat_query_batch_multi(nets, *hq[i][:3], out_h, hq[i][3], stream=stream, **opts)
+        if i >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    d2h = float(np.mean([4 * int(Vs[q.net].sum()) for q in qsets[args.warmup:]]))
+
+    # The same queries one at a time through eat_query (the plain single-query path).
+    q0 = qsets[-1]
+    plain_n = min(Q, args.plain_queries)
+    for i in range(8):
+        eat.eat_query(nets[q0.net[i]], int(q0.source[i]), int(q0.t_s[i]),
+                      torch.empty(int(Vs[q0.net[i]]), dtype=torch.int32, device="cuda"))
+    rows = {j: torch.empty(int(Vs[j]), dtype=torch.int32, device="cuda") for j in range(len(tts))}
+    t0 = time.perf_counter()
+    for i in range(plain_n):
+        j = int(q0.net[i])
+        eat.eat_query(nets[j], int(q0.source[i]), int(q0.t_s[i]), rows[j])
+    plain_s = time.perf_counter() - t0
+
+    times = torch.tensor([gpu_s, sum(e2e_t), plain_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    gpu_s, e2e_s, plain_s = times.tolist()
+    if rank != 0:
+        return 0
+    peak, peak_kind = measured_peak()
+    achieved = per_launch / (mean_ms / 1e3) / 1e9
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        scs = [oracle.SortedConnections(t) for t in tts]
+        threads = os.cpu_count() or 1
+        done, spent, used = 0, 0.0, threads
+        for q in qsets[args.warmup:]:
+            for j in range(len(tts)):
+                sel = np.nonzero(q.net == j)[0]
+                if sel.size == 0:
+                    continue
+                t0 = time.perf_counter()
+                _, used = oracle.csa_many(scs[j], q.source[sel], q.t_s[sel], threads)
+                spent += time.perf_counter() - t0
+                done += sel.size
+            if spent >= args.cpu_budget:
+                break
+        cpu = {"value": done / spent, "unit": "queries/s", "cores": used, "kind": "oracle",
+               "sample": f"{done} of the timed steps' queries (whole {Q}-query steps, grouped "
+                         f"by network), connection scan on {used} threads, {spent:.1f} s"}
+
+    n_q = Q * args.steps * world
+    line = {
+        "metric": "EAT queries/s (batched, ragged networks)",
+        "value": n_q / gpu_s, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": gpu_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "ragged64: 64 grid networks, stops log-uniform in [1,000, "
+                               "50,000], ceil(50 n / 1024) routes of 20 stops, headway 10-30 min",
+                   "global_batch": Q, "n_stops_total": int(Vs.sum()),
+                   "n_connections": int(sum(t.n_conn for t in tts)), "times": "int32 seconds",
+                   "l2": "flushed before every step (256 MB write)", "parallelism": "replicas",
+                   "method": "Cluster-AP fixpoint, one launch over all networks"},
+        "e2e": {"value": n_q / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 20 * Q,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} (burst copy)", "kernel": "eat_cta_kernel",
+                     "alg_bytes_per_launch": per_launch},
+        "cpu_baseline": cpu,
+        "sequential_plain_queries": {"value": plain_n / plain_s, "unit": "queries/s",
+                                     "queries": plain_n},
+        "cluster_width_s": args.cluster_width,
+        "work_per_query": {n: tot[n] / (Q * args.steps) for n in names},
+        "clocks": clocks.summary(), "kernel_hash": kernel_hash(), "build_s": t_build,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def workload(name: str, seed_offset: int = 0):
     if name == "city":
         return synth.city(seed_offset=seed_offset), BATCH
@@ -404,7 +568,9 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="city", choices=["city", "small", "large"])
+    ap.add_argument("--workload", default="city", choices=["city", "small", "large", "ragged"])
+    ap.add_argument("--plain-queries", type=int, default=4096,
+                    help="ragged workload: sequential single queries timed for comparison")
     ap.add_argument("--vwarp", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=10.0)
@@ -418,6 +584,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ragged":
+        return run_ours_ragged(args)
     return run_ours(args)
 
 

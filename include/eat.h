@@ -207,6 +207,52 @@ int32_t eat_version(void);
  */
 int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net **out);
 
+/* Pre-encoded input for eat_build_csr: the Cluster-AP structure itself (Section
+ * IV-A) for callers that encode their own timetable.  All arrays are host memory.
+ *   row_ptr[n_stops + 1]   types leaving stop u are row_ptr[u] .. row_ptr[u+1]-1
+ *                          (row_ptr[0] = 0, row_ptr[n_stops] = n_types)
+ *   type_v[n_types], type_dur[n_types]   head stop and duration (>= 1) of each
+ *                          connection type (Section III-B)
+ *   type_cl_ptr[n_types + 1]   clusters of type t are type_cl_ptr[t] ..
+ *                          type_cl_ptr[t+1]-1; every type has at least one
+ *   cl_k[n_clusters]       cluster index k: the cluster holds departures in
+ *                          [t0 + k * width, t0 + (k+1) * width) (Section III-D);
+ *                          strictly increasing within a type
+ *   cl_ap_ptr[n_clusters + 1]   APs of cluster c are cl_ap_ptr[c] .. cl_ap_ptr[c+1]-1;
+ *                          every cluster has at least one
+ *   ap_first[n_aps], ap_step[n_aps], ap_count[n_aps]   AP runs (Section II): terms
+ *                          first, first + step, ..., first + (count-1) * step, all
+ *                          inside the cluster's window; count >= 1, step >= 1 when
+ *                          count >= 2, step and count <= 65535; ordered by first
+ *                          term within a cluster */
+typedef struct {
+    int32_t n_stops;
+    int32_t n_types;
+    int64_t n_clusters;
+    int64_t n_aps;
+    const int32_t *row_ptr;
+    const int32_t *type_v;
+    const int32_t *type_dur;
+    const int64_t *type_cl_ptr;
+    const int32_t *cl_k;
+    const int64_t *cl_ap_ptr;
+    const int32_t *ap_first;
+    const int32_t *ap_step;
+    const int32_t *ap_count;
+} eat_csr_input;
+
+/*
+ * eat_build_csr -- build a network from pre-encoded connection types, clusters
+ * and AP runs (the layout of Section IV-A) instead of raw connections.  The
+ * input is validated and copied; opts->cluster_width and opts->t0 give the
+ * cluster windows (opts->subtrips must be EAT_SUBTRIPS_NONE).  Queries behave
+ * exactly as on a network built by eat_build from the connections the APs
+ * expand to.  n_conn in eat_stats is the total number of AP terms.
+ * Errors: EAT_ERR_INVALID (any inconsistency, with the first offending index),
+ * EAT_ERR_OOM, EAT_ERR_CUDA, EAT_ERR_NO_DEVICE.  On error *out is NULL.
+ */
+int eat_build_csr(const eat_csr_input *in, const eat_build_opts *opts, eat_net **out);
+
 /* Release a network and its device memory.  NULL is ignored.  No query on the
  * network may be in flight. */
 void eat_free(eat_net *net);
@@ -270,8 +316,12 @@ int eat_query_batch(const eat_net *net, const int32_t *sources, const int32_t *t
  *                1 <= n_nets <= EAT_MAX_NETS.
  *   net_idx, sources, times  [n] int32; arr_offsets [n] int64 (element offsets);
  *                host or device memory, all of the same kind.
- *   arr_out      device memory large enough for every row.
- * Asynchronous on `stream`.  Other arguments as eat_query_batch.
+ *   arr_out      device memory large enough for every row, or host memory when
+ *                the query arrays are host memory (then staged and copied back).
+ * Asynchronous on `stream` when every buffer is device memory, else returns
+ * after the rows are in arr_out.  One launch serves all queries: networks whose
+ * arrival row fits half an SM's shared memory keep it there, larger ones use
+ * their output row.  Other arguments as eat_query_batch.
  */
 #define EAT_MAX_NETS 128
 int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int32_t *net_idx,

@@ -80,7 +80,7 @@ static int device_info(int dev, DeviceInfo &out) {
         // Allow every CTA kernel the full opt-in shared memory (once per device).
         DeviceGuard guard(dev);
         for (int nets : {1, EAT_MAX_NETS})
-            for (int mem = 0; mem < 3; ++mem) {
+            for (int mem = 0; mem < 4; ++mem) {
                 e = cudaFuncSetAttribute(cta_kernel(nets, mem),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(d.smem_optin - d.reserve));
@@ -104,6 +104,7 @@ struct Plan {
     int32_t mask_words = 0;       // words per bitmap
     int32_t smem_mask_off = 0;    // int offsets into dynamic shared memory
     int32_t smem_q_off = 0;
+    int32_t smem_arr_cap = 0;     // mem 3: arrivals shared for networks up to this size
     int64_t spill_stride = 0;     // ints per persistent block
     int64_t mask_stride = 0;      // words per persistent block (global bitmaps only)
     size_t ws_bytes = 0;
@@ -115,7 +116,8 @@ static constexpr size_t kWsHeader = 256;   // work counter + internal status / c
 static constexpr size_t kQueueEntryBytes = 16;  // (stop, type) item x 2 buffers
 
 static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_query_opts *o,
-                     Plan &p) {
+                     Plan &p, int32_t vmin = -1) {
+    if (vmin < 0) vmin = vmax;
     DeviceInfo d;
     int rc = device_info(dev, d);
     if (rc) return rc;
@@ -147,12 +149,27 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
         return fail(EAT_ERR_INVALID, "arrivals do not fit in shared memory");
     if (place == EAT_PLACE_GLOBAL_ARR && !fits(1))
         return fail(EAT_ERR_INVALID, "bitmaps do not fit in shared memory");
-    if (place == EAT_PLACE_SHARED || (place == EAT_PLACE_AUTO && fits(0))) p.mem = 0;
+    // A batch over networks of uneven size whose largest arrival row would cost
+    // more than half an SM's shared memory keeps arrivals in shared memory only
+    // for the networks that fit half an SM (two blocks per SM stay resident).
+    const size_t half = d.smem_per_sm / 2 - d.reserve;
+    p.smem_arr_cap = 0;
+    if (place == EAT_PLACE_AUTO && vmin < vmax && base(0) + kQueueEntryBytes * qmin > half &&
+        fits(1)) {
+        const size_t room = half - base(1) - kQueueEntryBytes * 1024;
+        const int32_t cap = (int32_t)std::min<size_t>(room / 4 & ~(size_t)3, (size_t)vmax);
+        if (cap >= vmin) {
+            p.mem = 3;
+            p.smem_arr_cap = cap;
+        }
+    }
+    if (p.mem == 3) {
+    } else if (place == EAT_PLACE_SHARED || (place == EAT_PLACE_AUTO && fits(0))) p.mem = 0;
     else if (place == EAT_PLACE_GLOBAL_ARR || (place == EAT_PLACE_AUTO && fits(1))) p.mem = 1;
     else p.mem = 2;
 
     // Largest queue capacity that keeps the most blocks per SM the threads allow.
-    const size_t b0 = base(p.mem);
+    const size_t b0 = p.mem == 3 ? base(1) + (size_t)p.smem_arr_cap * 4 : base(p.mem);
     const int max_blocks = std::max(1, 2048 / p.block);
     p.qcap = (int32_t)qmin;
     for (int b = max_blocks; b >= 1; --b) {
@@ -164,8 +181,8 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
         p.qcap = (int32_t)std::max(cap, qmin);
         break;
     }
-    p.smem_mask_off = p.mem == 0 ? (int32_t)(arr_bytes / 4) : 0;
-    p.smem_q_off = p.smem_mask_off + (p.mem <= 1 ? 2 * p.mask_words : 0);
+    p.smem_mask_off = p.mem == 0 ? (int32_t)(arr_bytes / 4) : p.mem == 3 ? p.smem_arr_cap : 0;
+    p.smem_q_off = p.smem_mask_off + (p.mem != 2 ? 2 * p.mask_words : 0);
     p.smem = (size_t)p.smem_q_off * 4 + kQueueEntryBytes * (size_t)p.qcap;
 
     int per_sm = 0;
@@ -213,6 +230,7 @@ static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net
     qa.mask_words = p.mask_words;
     qa.smem_mask_off = p.smem_mask_off;
     qa.smem_q_off = p.smem_q_off;
+    qa.smem_arr_cap = p.smem_arr_cap;
     return qa;
 }
 
@@ -237,10 +255,13 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
                      const eat_query_opts *o, cudaStream_t st, int32_t *status_override,
                      eat_counters *counters_override) {
     const int dev = nets[0]->device;
-    int32_t vmax = 0;
-    for (int i = 0; i < n_nets; ++i) vmax = std::max(vmax, nets[i]->host.n_stops);
+    int32_t vmax = 0, vmin = INT32_MAX;
+    for (int i = 0; i < n_nets; ++i) {
+        vmax = std::max(vmax, nets[i]->host.n_stops);
+        vmin = std::min(vmin, nets[i]->host.n_stops);
+    }
     Plan p;
-    int rc = make_plan(dev, vmax, n, n_nets, o, p);
+    int rc = make_plan(dev, vmax, n, n_nets, o, p, vmin);
     if (rc) return rc;
     if (ws_bytes < p.ws_bytes)
         return fail(EAT_ERR_WORKSPACE, "workspace of " + std::to_string(ws_bytes) +
@@ -269,6 +290,67 @@ extern "C" {
 const char *eat_last_error(void) { return g_err.c_str(); }
 
 int32_t eat_version(void) { return 100; }
+
+}  // extern "C"
+
+namespace eat {
+
+// Upload a built network (logical arrays already in net->host) to its device.
+static int upload(eat_net *net) {
+    int rc = build_fused(net->host);
+    if (rc) return rc;
+    if (net->device < 0) return EAT_OK;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || net->device >= count) {
+        cudaGetLastError();
+        return fail(EAT_ERR_NO_DEVICE, "no CUDA device " + std::to_string(net->device));
+    }
+    const HostNet &h = net->host;
+    size_t off_row = 0;
+    size_t off_ty = align_up(off_row + ((size_t)h.n_stops + 1) * 4, 256);
+    size_t off_ce = align_up(off_ty + h.ty_dev.size() * 4, 256);
+    size_t off_apx = align_up(off_ce + h.ce.size() * 4, 256);
+    size_t total = align_up(off_apx + h.apx.size() * 4 + 16, 256);
+    DeviceGuard guard(net->device);
+    if (!guard.ok) return fail(EAT_ERR_NO_DEVICE, "cudaSetDevice failed");
+    e = cudaMalloc(&net->blob, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        net->blob = nullptr;
+        return fail(EAT_ERR_OOM, "cudaMalloc of the network failed");
+    }
+    net->blob_bytes = (int64_t)total;
+    char *b = (char *)net->blob;
+    struct Piece { size_t off; const void *src; size_t bytes; } pieces[] = {
+        {off_row, h.row_ptr.data(), h.row_ptr.size() * 4},
+        {off_ty, h.ty_dev.data(), h.ty_dev.size() * 4},
+        {off_ce, h.ce.data(), h.ce.size() * 4},
+        {off_apx, h.apx.data(), h.apx.size() * 4},
+    };
+    for (const Piece &pc : pieces) {
+        if (!pc.bytes) continue;
+        e = cudaMemcpy(b + pc.off, pc.src, pc.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy of the network");
+    }
+    NetDev &d = net->dev;
+    d.row_ptr = (const int32_t *)(b + off_row);
+    d.ty = (const int4 *)(b + off_ty);
+    d.ce = (const int4 *)(b + off_ce);
+    d.apx = (const uint2 *)(b + off_apx);
+    d.n_stops = h.n_stops;
+    d.n_types = h.n_types;
+    d.t0 = h.t0;
+    d.width = h.width;
+    d.inv_width = 1.0f / (float)h.width;
+    d.k_min = h.k_min;
+    d.y = h.y;
+    return EAT_OK;
+}
+
+}  // namespace eat
+
+extern "C" {
 
 int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net **out) {
     clear_error();
@@ -299,66 +381,34 @@ int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net *
     } else {
         rc = build_host(conn, width, o.t0, net->host);
     }
-    if (!rc) rc = build_fused(net->host);
+    net->device = o.device;
+    if (!rc) rc = upload(net);
     if (rc) {
-        delete net;
+        eat_free(net);
         return rc;
     }
+    *out = net;
+    return EAT_OK;
+}
+
+int eat_build_csr(const eat_csr_input *in, const eat_build_opts *opts, eat_net **out) {
+    clear_error();
+    if (!out) return fail(EAT_ERR_INVALID, "out must not be NULL");
+    *out = nullptr;
+    if (!in) return fail(EAT_ERR_INVALID, "input must not be NULL");
+    eat_build_opts o{};
+    if (opts) o = *opts;
+    if (o.subtrips != EAT_SUBTRIPS_NONE)
+        return fail(EAT_ERR_INVALID, "sub-trips need raw connections (use eat_build)");
+    const int32_t width = o.cluster_width ? o.cluster_width : 3600;
+    eat_net *net = new (std::nothrow) eat_net();
+    if (!net) return fail(EAT_ERR_OOM, "host allocation failed");
+    int rc = build_host_csr(in, width, o.t0, net->host);
     net->device = o.device;
-    if (o.device >= 0) {
-        int count = 0;
-        cudaError_t e = cudaGetDeviceCount(&count);
-        if (e != cudaSuccess || o.device >= count) {
-            cudaGetLastError();
-            delete net;
-            return fail(EAT_ERR_NO_DEVICE, "no CUDA device " + std::to_string(o.device));
-        }
-        const HostNet &h = net->host;
-        size_t off_row = 0;
-        size_t off_ty = align_up(off_row + ((size_t)h.n_stops + 1) * 4, 256);
-        size_t off_ce = align_up(off_ty + h.ty_dev.size() * 4, 256);
-        size_t off_apx = align_up(off_ce + h.ce.size() * 4, 256);
-        size_t total = align_up(off_apx + h.apx.size() * 4 + 16, 256);
-        DeviceGuard guard(o.device);
-        if (!guard.ok) {
-            delete net;
-            return fail(EAT_ERR_NO_DEVICE, "cudaSetDevice failed");
-        }
-        e = cudaMalloc(&net->blob, total);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            delete net;
-            return fail(EAT_ERR_OOM, "cudaMalloc of the network failed");
-        }
-        net->blob_bytes = (int64_t)total;
-        char *b = (char *)net->blob;
-        struct Piece { size_t off; const void *src; size_t bytes; } pieces[] = {
-            {off_row, h.row_ptr.data(), h.row_ptr.size() * 4},
-            {off_ty, h.ty_dev.data(), h.ty_dev.size() * 4},
-            {off_ce, h.ce.data(), h.ce.size() * 4},
-            {off_apx, h.apx.data(), h.apx.size() * 4},
-        };
-        for (const Piece &pc : pieces) {
-            if (!pc.bytes) continue;
-            e = cudaMemcpy(b + pc.off, pc.src, pc.bytes, cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) {
-                cudaFree(net->blob);
-                delete net;
-                return cuda_fail(e, "cudaMemcpy of the network");
-            }
-        }
-        NetDev &d = net->dev;
-        d.row_ptr = (const int32_t *)(b + off_row);
-        d.ty = (const int4 *)(b + off_ty);
-        d.ce = (const int4 *)(b + off_ce);
-        d.apx = (const uint2 *)(b + off_apx);
-        d.n_stops = h.n_stops;
-        d.n_types = h.n_types;
-        d.t0 = h.t0;
-        d.width = h.width;
-        d.inv_width = 1.0f / (float)h.width;
-        d.k_min = h.k_min;
-        d.y = h.y;
+    if (!rc) rc = upload(net);
+    if (rc) {
+        eat_free(net);
+        return rc;
     }
     *out = net;
     return EAT_OK;
@@ -416,13 +466,14 @@ size_t eat_workspace_bytes(const eat_net *const *nets, int32_t n_nets, int32_t n
                            const eat_query_opts *opts) {
     clear_error();
     if (!nets || n_nets < 1 || n_nets > EAT_MAX_NETS || n < 0) return 0;
-    int32_t vmax = 0;
+    int32_t vmax = 0, vmin = INT32_MAX;
     for (int i = 0; i < n_nets; ++i) {
         if (!nets[i] || nets[i]->device < 0 || nets[i]->device != nets[0]->device) return 0;
         vmax = std::max(vmax, nets[i]->host.n_stops);
+        vmin = std::min(vmin, nets[i]->host.n_stops);
     }
     Plan p;
-    if (make_plan(nets[0]->device, vmax, n, n_nets, opts, p)) return 0;
+    if (make_plan(nets[0]->device, vmax, n, n_nets, opts, p, vmin)) return 0;
     return p.ws_bytes;
 }
 
@@ -481,13 +532,15 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
     if (n < 0) return fail(EAT_ERR_INVALID, "n must be >= 0");
     if (n > 0 && (!net_idx || !sources || !times || !arr_out || !arr_offsets))
         return fail(EAT_ERR_INVALID, "NULL query array");
-    if (n > 0 && !is_device_ptr(arr_out)) return fail(EAT_ERR_INVALID, "arr_out must be device memory");
     DeviceGuard guard(nets[0]->device);
     cudaStream_t st = (cudaStream_t)stream;
     const bool dev_in = n == 0 || is_device_ptr(sources);
+    const bool dev_out = n == 0 || is_device_ptr(arr_out);
     if (n > 0 && (is_device_ptr(net_idx) != dev_in || is_device_ptr(times) != dev_in ||
                   is_device_ptr(arr_offsets) != dev_in))
         return fail(EAT_ERR_INVALID, "query arrays must all be host or all device memory");
+    if (!dev_out && dev_in)
+        return fail(EAT_ERR_INVALID, "a host arr_out needs host query arrays");
     if (dev_in) {
         if (!workspace) {
             std::lock_guard<std::mutex> g(nets[0]->ws_lock);
@@ -501,15 +554,19 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
         return run_batch(nets, n_nets, net_idx, sources, times, n, arr_out, arr_offsets, workspace,
                          workspace_bytes, opts, st, nullptr, nullptr);
     }
-    // Host query arrays: validate here, stage them through device memory.
+    // Host query arrays: validate here, stage them (and a host arr_out) through device memory.
+    int64_t out_elems = 0;
     for (int32_t i = 0; i < n; ++i) {
         if (net_idx[i] < 0 || net_idx[i] >= n_nets) return fail(EAT_ERR_INVALID, "net_idx out of range");
         if (sources[i] < 0 || sources[i] >= nets[net_idx[i]]->host.n_stops)
             return fail(EAT_ERR_INVALID, "source out of range");
+        if (arr_offsets[i] < 0) return fail(EAT_ERR_INVALID, "negative arr_offsets entry");
+        out_elems = std::max(out_elems, arr_offsets[i] + nets[net_idx[i]]->host.n_stops);
     }
     std::lock_guard<std::mutex> g(nets[0]->ws_lock);
     const size_t in_bytes = align_up((size_t)n * 4, 256) * 3 + align_up((size_t)n * 8, 256);
-    int rc = ensure_buffer(nets[0]->stage, nets[0]->stage_bytes, in_bytes);
+    const size_t out_bytes = dev_out ? 0 : (size_t)out_elems * 4;
+    int rc = ensure_buffer(nets[0]->stage, nets[0]->stage_bytes, in_bytes + out_bytes);
     if (rc) return rc;
     char *sb = (char *)nets[0]->stage;
     int32_t *d_idx = (int32_t *)sb;
@@ -531,11 +588,13 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
         ws = nets[0]->ws;
         wsb = nets[0]->ws_bytes;
     }
-    rc = run_batch(nets, n_nets, d_idx, d_src, d_ts, n, arr_out, d_off, ws, wsb, opts, st,
+    int32_t *out_d = dev_out ? arr_out : (int32_t *)(sb + in_bytes);
+    rc = run_batch(nets, n_nets, d_idx, d_src, d_ts, n, out_d, d_off, ws, wsb, opts, st,
                    nullptr, nullptr);
     if (rc) return rc;
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (!dev_out) e = cudaMemcpyAsync(arr_out, out_d, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "eat_query_batch_multi");
     return EAT_OK;
 }
 

@@ -278,6 +278,106 @@ int build_host(const eat_connections *c, int32_t width, int32_t t0, HostNet &h) 
     return EAT_OK;
 }
 
+// Pre-encoded input (eat_build_csr): validate and convert to the logical arrays.
+int build_host_csr(const eat_csr_input *in, int32_t width, int32_t t0, HostNet &h) {
+    const int32_t V = in->n_stops, T = in->n_types;
+    const int64_t NC = in->n_clusters, NA = in->n_aps;
+    auto bad = [](const std::string &what, int64_t i) {
+        return fail(EAT_ERR_INVALID, what + " (index " + std::to_string(i) + ")");
+    };
+    if (V <= 0) return fail(EAT_ERR_INVALID, "n_stops must be >= 1");
+    if (T < 0 || NC < 0 || NA < 0) return fail(EAT_ERR_INVALID, "negative sizes");
+    if (width < 1 || width > 65535) return fail(EAT_ERR_INVALID, "cluster_width must be in 1..65535");
+    if (!in->row_ptr || (T > 0 && (!in->type_v || !in->type_dur || !in->type_cl_ptr)) ||
+        (NC > 0 && (!in->cl_k || !in->cl_ap_ptr)) ||
+        (NA > 0 && (!in->ap_first || !in->ap_step || !in->ap_count)))
+        return fail(EAT_ERR_INVALID, "NULL input array");
+    if (NC >= INT32_MAX || NA >= INT32_MAX) return fail(EAT_ERR_INVALID, "too many clusters or APs");
+    if (in->row_ptr[0] != 0 || in->row_ptr[V] != T) return fail(EAT_ERR_INVALID, "row_ptr must run from 0 to n_types");
+    for (int32_t u = 0; u < V; ++u)
+        if (in->row_ptr[u + 1] < in->row_ptr[u]) return bad("row_ptr decreases", u);
+    if (T > 0 && (in->type_cl_ptr[0] != 0 || in->type_cl_ptr[T] != NC))
+        return fail(EAT_ERR_INVALID, "type_cl_ptr must run from 0 to n_clusters");
+    if (NC > 0 && (in->cl_ap_ptr[0] != 0 || in->cl_ap_ptr[NC] != NA))
+        return fail(EAT_ERR_INVALID, "cl_ap_ptr must run from 0 to n_aps");
+    h = HostNet();
+    h.n_stops = V;
+    h.n_types = T;
+    h.width = width;
+    h.t0 = t0;
+    try {
+        h.row_ptr.assign(in->row_ptr, in->row_ptr + (size_t)V + 1);
+        h.type_rec.resize((size_t)T * 4);
+        h.type_cl.resize((size_t)T);
+        h.ap.reserve((size_t)NA * 2);
+    } catch (const std::bad_alloc &) {
+        return fail(EAT_ERR_OOM, "host allocation failed");
+    }
+    int32_t last_u = -1;
+    for (int32_t u = 0; u < V; ++u) {
+        const int32_t deg = in->row_ptr[u + 1] - in->row_ptr[u];
+        h.max_out_types = std::max(h.max_out_types, deg);
+        (void)last_u;
+    }
+    for (int32_t t = 0; t < T; ++t) {
+        const int32_t v = in->type_v[t], lam = in->type_dur[t];
+        if (v < 0 || v >= V) return bad("type head stop out of range", t);
+        if (lam < 1) return bad("type duration must be >= 1", t);
+        const int64_t c0 = in->type_cl_ptr[t], c1 = in->type_cl_ptr[t + 1];
+        if (c1 <= c0) return bad("type without clusters", t);
+        int32_t first = EAT_INF, last = INT32_MIN;
+        int32_t prev_k = INT32_MIN;
+        const int32_t cl_start = (int32_t)h.cl.size();
+        int32_t k_first = 0;
+        for (int64_t c = c0; c < c1; ++c) {
+            const int32_t k = in->cl_k[c];
+            if (k < 0) return bad("cluster index must be >= 0", c);
+            if (c > c0 && k <= prev_k) return bad("cluster indices must increase within a type", c);
+            const int64_t lo = (int64_t)t0 + (int64_t)k * width, hi = lo + width;
+            if (hi - 1 >= (int64_t)INT32_MAX) return bad("cluster window overflows int32", c);
+            if (c == c0) k_first = k;
+            // empty clusters between the previous one and k
+            for (int32_t kk = (c == c0 ? k : prev_k + 1); kk < k; ++kk)
+                h.cl.push_back((int32_t)(h.ap.size() / 2));
+            h.cl.push_back((int32_t)(h.ap.size() / 2));
+            const int64_t a0 = in->cl_ap_ptr[c], a1 = in->cl_ap_ptr[c + 1];
+            if (a1 <= a0) return bad("cluster without APs", c);
+            int32_t prev_first = INT32_MIN;
+            for (int64_t a = a0; a < a1; ++a) {
+                const int32_t f = in->ap_first[a], st = in->ap_step[a], n = in->ap_count[a];
+                if (n < 1 || n > 65535) return bad("AP term count must be in 1..65535", a);
+                if (n >= 2 && (st < 1 || st > 65535)) return bad("AP difference must be in 1..65535", a);
+                const int64_t lt = (int64_t)f + (int64_t)(n - 1) * (n >= 2 ? st : 0);
+                if (f < lo || lt >= hi) return bad("AP terms outside the cluster window", a);
+                if (lt + lam >= (int64_t)INT32_MAX) return bad("arrival overflows int32", a);
+                if (a > a0 && f < prev_first) return bad("APs must be ordered by first term", a);
+                prev_first = f;
+                first = std::min(first, f);
+                last = std::max(last, (int32_t)lt);
+                h.ap.push_back((uint32_t)f);
+                h.ap.push_back(((uint32_t)(n >= 2 ? st : 0) << 16) | (uint32_t)n);
+                h.n_conn += n;
+            }
+            prev_k = k;
+        }
+        h.cl.push_back((int32_t)(h.ap.size() / 2));
+        h.type_rec[4 * (size_t)t] = v;
+        h.type_rec[4 * (size_t)t + 1] = lam;
+        h.type_rec[4 * (size_t)t + 2] = first;
+        h.type_rec[4 * (size_t)t + 3] = last;
+        h.type_cl[t] = cl_start - k_first;
+        h.max_clusters = std::max(h.max_clusters, prev_k - k_first + 1);
+        if ((int64_t)h.cl.size() >= INT32_MAX) return fail(EAT_ERR_INVALID, "too many clusters");
+    }
+    // distinct (u, v) pairs
+    for (int32_t u = 0; u < V; ++u) {
+        std::vector<int32_t> heads(in->type_v + in->row_ptr[u], in->type_v + in->row_ptr[u + 1]);
+        std::sort(heads.begin(), heads.end());
+        h.n_edges += (int32_t)(std::unique(heads.begin(), heads.end()) - heads.begin());
+    }
+    return EAT_OK;
+}
+
 // Sub-trips (Section III-G).  A trip of k connections, ordered by departure, is cut
 // into consecutive sub-trips of r connections (the last one shorter); r is the
 // nearest integer to sqrt(k) (EAT_SUBTRIPS_SQRT_K) or to the square root of the

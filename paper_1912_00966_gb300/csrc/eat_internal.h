@@ -97,6 +97,9 @@ int add_subtrips(const eat_connections *c, int32_t scheme, std::vector<int32_t> 
                  std::vector<int32_t> &v, std::vector<int32_t> &dep, std::vector<int32_t> &dur,
                  int64_t &n_added);
 
+// Logical arrays from pre-encoded types / clusters / APs (eat_build.cpp).
+int build_host_csr(const eat_csr_input *in, int32_t width, int32_t t0, HostNet &h);
+
 // Device layout from the logical arrays (eat_build.cpp).
 int build_fused(HostNet &h);
 

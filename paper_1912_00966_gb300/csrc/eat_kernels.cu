@@ -27,8 +27,10 @@
 // Stops whose items do not fit spill to a global queue and are expanded by
 // `vwarp`-lane sub-warps (Section III-F's virtual warps).
 //
-// Buffers per query: arrivals in shared memory when they fit (SMEM_ARR), else
-// the output row; two frontier bitmaps (this round's pushes, last round's) in
+// Buffers per query: arrivals in shared memory (ARR = kArrShared), in the
+// output row (kArrGlobal), or per query whichever the query's network allows
+// (kArrPerQuery: shared when n_stops <= smem_arr_cap, for batches over networks
+// of uneven size); two frontier bitmaps (this round's pushes, last round's) in
 // shared memory when they fit (SMEM_MASK).
 #include <cuda_runtime.h>
 
@@ -126,16 +128,19 @@ __device__ __forceinline__ int32_t next_departure(const NetDev &N, int32_t t, in
     return cluster_lookup(__ldg(c), __ldg(c + 1), e, N.apx, aps);
 }
 
-template <bool SMEM_ARR>
-__device__ __forceinline__ int32_t load_arr(const int32_t *arr, int32_t i) {
-    if (SMEM_ARR) return *((const volatile int32_t *)arr + i);
+enum { kArrGlobal = 0, kArrShared = 1, kArrPerQuery = 2 };
+
+// Arrival load that sees the block's own atomics: shared memory through a
+// volatile read, global memory from L2 (not a possibly stale L1 line).
+__device__ __forceinline__ int32_t load_arr(const int32_t *arr, int32_t i, bool shared) {
+    if (shared) return *((const volatile int32_t *)arr + i);
     return __ldcg(arr + i);
 }
 
 constexpr int32_t kNullItem = -1;           // hole left by a stop that spilled
 constexpr int32_t kFirstItem = INT32_MIN;    // flag on the first item of a stop
 
-template <int NETS, bool SMEM_ARR, bool SMEM_MASK>
+template <int NETS, int ARR, bool SMEM_MASK>
 __global__ void __launch_bounds__(1024, 1)
 eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) {
     extern __shared__ __align__(16) int32_t smem[];
@@ -171,7 +176,8 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
         const int32_t V = N.n_stops;
         const int64_t off = qa.arr_off ? __ldg(qa.arr_off + q) : (int64_t)q * V;
         int32_t *const out = qa.arr_out + off;
-        int32_t *const arr = SMEM_ARR ? smem : out;
+        const bool arr_shared = ARR == kArrShared || (ARR == kArrPerQuery && V <= qa.smem_arr_cap);
+        int32_t *const arr = arr_shared ? smem : out;
         const int32_t nwords = (V + 31) >> 5;
         uint32_t *const mask0 = mask_base;
         uint32_t *const mask1 = mask_base + qa.mask_words;
@@ -231,7 +237,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                 ++c_evals;
                 const int32_t v = ty.x;
                 const int32_t cand = tc + ty.y;
-                if (cand >= load_arr<SMEM_ARR>(arr, v)) return;
+                if (cand >= load_arr(arr, v, arr_shared)) return;
                 const int32_t old = atomicMin(arr + v, cand);
                 if (cand >= old) return;
                 ++c_relax;
@@ -262,7 +268,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                     atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
                     ++c_vert;
                 }
-                const int32_t e_u = load_arr<SMEM_ARR>(arr, u);
+                const int32_t e_u = load_arr(arr, u, arr_shared);
                 const int32_t k = cluster_slot(N, e_u);
                 if (k >= N.y) {                             // no departure left anywhere
                     ++c_types;
@@ -279,7 +285,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                     atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
                     ++c_vert;
                 }
-                const int32_t e_u = load_arr<SMEM_ARR>(arr, u);
+                const int32_t e_u = load_arr(arr, u, arr_shared);
                 const int32_t k = cluster_slot(N, e_u);
                 if (k >= N.y) {
                     if (lane == 0) c_types += end - beg;
@@ -295,7 +301,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
         }
         const int32_t F = n_items + n_spill;
 
-        if (SMEM_ARR) {
+        if (arr_shared) {
             __syncthreads();
             for (int32_t i = tid; i < V; i += nthr) out[i] = arr[i];
         }
@@ -343,9 +349,10 @@ __global__ void eat_next_departure_kernel(const NetDev N, const int32_t *types,
 template <int NETS>
 static const void *cta_kernel_ptr(int mem) {
     switch (mem) {
-    case 0: return (const void *)eat_cta_kernel<NETS, true, true>;
-    case 1: return (const void *)eat_cta_kernel<NETS, false, true>;
-    default: return (const void *)eat_cta_kernel<NETS, false, false>;
+    case 0: return (const void *)eat_cta_kernel<NETS, kArrShared, true>;
+    case 1: return (const void *)eat_cta_kernel<NETS, kArrGlobal, true>;
+    case 3: return (const void *)eat_cta_kernel<NETS, kArrPerQuery, true>;
+    default: return (const void *)eat_cta_kernel<NETS, kArrGlobal, false>;
     }
 }
 
@@ -360,9 +367,10 @@ static cudaError_t launch_cta_t(const NetDev *nets, int n_nets, const QueryArgs 
     for (int i = 0; i < n_nets && i < NETS; ++i) tab.net[i] = nets[i];
     for (int i = n_nets; i < NETS; ++i) tab.net[i] = NetDev{};
     switch (mem) {
-    case 0: eat_cta_kernel<NETS, true, true><<<grid, block, smem, st>>>(tab, qa); break;
-    case 1: eat_cta_kernel<NETS, false, true><<<grid, block, smem, st>>>(tab, qa); break;
-    default: eat_cta_kernel<NETS, false, false><<<grid, block, smem, st>>>(tab, qa); break;
+    case 0: eat_cta_kernel<NETS, kArrShared, true><<<grid, block, smem, st>>>(tab, qa); break;
+    case 1: eat_cta_kernel<NETS, kArrGlobal, true><<<grid, block, smem, st>>>(tab, qa); break;
+    case 3: eat_cta_kernel<NETS, kArrPerQuery, true><<<grid, block, smem, st>>>(tab, qa); break;
+    default: eat_cta_kernel<NETS, kArrGlobal, false><<<grid, block, smem, st>>>(tab, qa); break;
     }
     return cudaGetLastError();
 }

@@ -29,10 +29,12 @@ struct QueryArgs {
     int32_t mask_words;        // words per bitmap (padded)
     int32_t smem_mask_off;     // int offset of the bitmaps in dynamic shared memory
     int32_t smem_q_off;        // int offset of the item buffers in dynamic shared memory
+    int32_t smem_arr_cap;      // per-query placement: arrivals shared when n_stops <= this
 };
 
-// mem: 0 = arrivals and bitmap in shared memory, 1 = arrivals global / bitmap
-// shared, 2 = both global.  nets: 1 or EAT_MAX_NETS (kernel table size).
+// mem: 0 = arrivals and bitmaps in shared memory, 1 = arrivals global / bitmaps
+// shared, 2 = both global, 3 = bitmaps shared and arrivals shared per query when
+// the query's network fits.  nets: 1 or EAT_MAX_NETS (kernel table size).
 const void *cta_kernel(int nets, int mem);
 cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
                        int block, size_t smem, cudaStream_t st);

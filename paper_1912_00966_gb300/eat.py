@@ -42,6 +42,14 @@ class eat_build_opts(ctypes.Structure):
                 ("device", ctypes.c_int32), ("subtrips", ctypes.c_int32)]
 
 
+class eat_csr_input(ctypes.Structure):
+    _fields_ = [("n_stops", ctypes.c_int32), ("n_types", ctypes.c_int32),
+                ("n_clusters", ctypes.c_int64), ("n_aps", ctypes.c_int64),
+                ("row_ptr", _vp), ("type_v", _vp), ("type_dur", _vp), ("type_cl_ptr", _vp),
+                ("cl_k", _vp), ("cl_ap_ptr", _vp), ("ap_first", _vp), ("ap_step", _vp),
+                ("ap_count", _vp)]
+
+
 class eat_stats(ctypes.Structure):
     _fields_ = [("n_stops", ctypes.c_int32), ("n_types", ctypes.c_int32),
                 ("n_edges", ctypes.c_int32), ("cluster_width", ctypes.c_int32),
@@ -86,6 +94,8 @@ _sig("eat_last_error", ctypes.c_char_p, [])
 _sig("eat_version", ctypes.c_int32, [])
 _sig("eat_build", ctypes.c_int, [ctypes.POINTER(eat_connections), ctypes.POINTER(eat_build_opts),
                                  ctypes.POINTER(_vp)])
+_sig("eat_build_csr", ctypes.c_int, [ctypes.POINTER(eat_csr_input), ctypes.POINTER(eat_build_opts),
+                                     ctypes.POINTER(_vp)])
 _sig("eat_free", None, [_vp])
 _sig("eat_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(eat_stats)])
 _sig("eat_net_host_view", ctypes.c_int, [_vp, ctypes.POINTER(eat_net_view)])
@@ -101,7 +111,7 @@ _sig("eat_next_departure", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, _v
 _sig("eat_query_batch_noalloc", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp,
                                                ctypes.POINTER(eat_query_opts), _vp])
 
-EXPORTED = ("eat_last_error", "eat_version", "eat_build", "eat_free", "eat_get_stats",
+EXPORTED = ("eat_last_error", "eat_version", "eat_build", "eat_build_csr", "eat_free", "eat_get_stats",
             "eat_net_host_view", "eat_query", "eat_workspace_bytes", "eat_query_batch",
             "eat_query_batch_multi", "eat_next_departure", "eat_query_batch_noalloc")
 
@@ -192,6 +202,20 @@ def eat_build(n_stops, u, v, dep, dur, cluster_width=0, t0=0, device=0, trip=Non
     h = _vp()
     _check(_lib.eat_build(ctypes.byref(c), ctypes.byref(o), ctypes.byref(h)), "eat_build")
     return Net(h.value)
+
+
+def eat_build_csr(n_stops, row_ptr, type_v, type_dur, type_cl_ptr, cl_k, cl_ap_ptr, ap_first,
+                  ap_step, ap_count, cluster_width=0, t0=0, device=0) -> Net:
+    """Build from pre-encoded connection types, clusters and AP runs (see eat.h)."""
+    i64 = lambda a: np.ascontiguousarray(a, dtype=np.int64)
+    arrs = [_i32(row_ptr), _i32(type_v), _i32(type_dur), i64(type_cl_ptr), _i32(cl_k),
+            i64(cl_ap_ptr), _i32(ap_first), _i32(ap_step), _i32(ap_count)]
+    c = eat_csr_input(int(n_stops), int(arrs[1].shape[0]), int(arrs[4].shape[0]),
+                      int(arrs[6].shape[0]), *[a.ctypes.data for a in arrs])
+    o = eat_build_opts(int(cluster_width), int(t0), int(device), 0)
+    h = _vp()
+    _check(_lib.eat_build_csr(ctypes.byref(c), ctypes.byref(o), ctypes.byref(h)), "eat_build_csr")
+    return Net(h.value, keep=arrs)
 
 
 def eat_free(net: Net) -> None:

@@ -271,3 +271,74 @@ def test_subtrips_leave_earliest_arrivals_unchanged(scheme):
     ra, _ = oracle.csa_many(a, q.source, q.t_s, 4)
     rb, _ = oracle.csa_many(b, q.source, q.t_s, 4)
     assert np.array_equal(ra, rb)
+
+
+# ------------------------------------------------------------------ pre-encoded input (eat_build_csr)
+
+def csr_from_view(net):
+    """The pre-encoded (types, clusters, AP runs) arrays of a built network."""
+    hv, st = eat.eat_net_host_view(net), eat.eat_get_stats(net)
+    rp, rec, clb, cl, ap = hv["row_ptr"], hv["type_rec"], hv["type_cl"], hv["cl"], hv["ap"]
+    W, t0 = st["cluster_width"], st["t0"]
+    type_cl_ptr, cl_k, cl_ap_ptr, first, step, count = [0], [], [0], [], [], []
+    for t in range(st["n_types"]):
+        f, l = int(rec[t][2]), int(rec[t][3])
+        for k in range((f - t0) // W, (l - t0) // W + 1):
+            lo, hi = int(cl[clb[t] + k]), int(cl[clb[t] + k + 1])
+            if hi == lo:
+                continue
+            cl_k.append(k)
+            for a in range(lo, hi):
+                first.append(int(ap[a, 0]))
+                step.append(int(ap[a, 1]) >> 16)
+                count.append(int(ap[a, 1]) & 0xFFFF)
+            cl_ap_ptr.append(len(first))
+        type_cl_ptr.append(len(cl_k))
+    return dict(n_stops=st["n_stops"], row_ptr=rp, type_v=rec[:, 0], type_dur=rec[:, 1],
+                type_cl_ptr=type_cl_ptr, cl_k=cl_k, cl_ap_ptr=cl_ap_ptr, ap_first=first,
+                ap_step=step, ap_count=count)
+
+
+@pytest.mark.parametrize("make,width", [(synth.small_grid, 3600), (synth.small_grid, 900),
+                                        (lambda: synth.tiny_random(9, 400, 3, t_max=20000), 3600)])
+def test_build_csr_round_trip(make, width):
+    tt = make()
+    a = _build(tt, cluster_width=width)
+    b = eat.eat_build_csr(**csr_from_view(a), cluster_width=width, device=-1)
+    va, vb = eat.eat_net_host_view(a), eat.eat_net_host_view(b)
+    for k in ("row_ptr", "type_rec", "cl", "ap", "cluster_entries", "ap_extra"):
+        assert np.array_equal(va[k], vb[k]), k
+    sa, sb = eat.eat_get_stats(a), eat.eat_get_stats(b)
+    for k in ("n_types", "n_edges", "n_ap", "y", "k_min", "max_out_types"):
+        assert sa[k] == sb[k], k
+
+
+def test_build_csr_paper_example():
+    # Section III-C: departures 8:00, 8:15, ..., 18:00 as one AP when one cluster spans them.
+    net = eat.eat_build_csr(2, [0, 1, 1], [1], [60], [0, 1], [0], [0, 1], [28800], [900], [41],
+                            cluster_width=65535, device=-1)
+    st = eat.eat_get_stats(net)
+    assert st["n_types"] == 1 and st["n_conn"] == 41 and st["n_ap"] == 1
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("ap_first", [3599], "outside"), ("ap_count", [0], "count"), ("ap_step", [0], "difference"),
+    ("type_dur", [0], "duration"), ("type_v", [5], "head stop"), ("row_ptr", [0, 2, 1], "row_ptr"),
+    ("cl_k", [-1], "cluster index"),
+])
+def test_build_csr_rejects_bad_input(field, value, msg):
+    args = dict(n_stops=2, row_ptr=[0, 1, 1], type_v=[1], type_dur=[60], type_cl_ptr=[0, 1],
+                cl_k=[1], cl_ap_ptr=[0, 1], ap_first=[3600], ap_step=[600], ap_count=[6])
+    eat.eat_build_csr(**args, device=-1)          # the unmodified input is valid
+    args[field] = value
+    with pytest.raises(eat.EatError) as ei:
+        eat.eat_build_csr(**args, device=-1)
+    assert ei.value.code == eat.EAT_ERR_INVALID and msg in str(ei.value)
+
+
+def test_build_csr_rejects_unsorted_aps():
+    args = dict(n_stops=2, row_ptr=[0, 1, 1], type_v=[1], type_dur=[60], type_cl_ptr=[0, 1],
+                cl_k=[1], cl_ap_ptr=[0, 2], ap_first=[4000, 3700], ap_step=[0, 0], ap_count=[1, 1])
+    with pytest.raises(eat.EatError) as ei:
+        eat.eat_build_csr(**args, device=-1)
+    assert "ordered" in str(ei.value)

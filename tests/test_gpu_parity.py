@@ -315,3 +315,37 @@ def test_subtrips_small_grid_all_queries(eat, small):
     assert np.array_equal(got, small.oracle_rows(q.source, q.t_s))
     for s_, t_ in [(0, 28800), (0, 0), (5, 86000)]:
         assert np.array_equal(eat.eat_query(enh.net, s_, t_), oracle.csa(small.sc, s_, t_))
+
+
+def test_build_csr_network_parity(eat, city):
+    """A network built from pre-encoded types, clusters and AP runs answers like eat_build's."""
+    from test_build_host import csr_from_view
+    host = eat.eat_build(city.tt.n_stops, city.tt.u, city.tt.v, city.tt.dep, city.tt.dur, device=-1)
+    net = eat.eat_build_csr(**csr_from_view(host), device=0)
+    q = synth.random_queries(city.tt, 128, 0xC5)
+    out = torch.empty(128 * city.V, dtype=torch.int32, device="cuda")
+    eat.eat_query_batch(net, _dev(q.source), _dev(q.t_s), out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.view(128, city.V).cpu().numpy(), city.oracle_rows(q.source, q.t_s))
+
+
+def test_ragged_batch_with_per_query_placement(eat, small):
+    """A 60,000-stop network next to small ones: one launch, arrivals in shared memory for
+    the networks that fit and in the output row for the others; host output staged."""
+    big_tt = synth.grid_timetable(60000, int(np.ceil(50 * 60000 / 1024)), 4242, force_stop0=False)
+    nets = [small, Case(eat, synth.grid_timetable(5000, 245, 77, force_stop0=False)), Case(eat, big_tt)]
+    Q = 120
+    qs = synth.random_queries([c.tt for c in nets], Q, 9)
+    sizes = np.array([nets[i].V for i in qs.net], np.int64)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    out = np.full(int(sizes.sum()), -7, dtype=np.int32)
+    eat.eat_query_batch_multi([c.net for c in nets], qs.net, qs.source, qs.t_s, out, offs)
+    for i in range(Q):
+        c = nets[qs.net[i]]
+        assert np.array_equal(out[offs[i]:offs[i] + c.V],
+                              oracle.csa(c.sc, int(qs.source[i]), int(qs.t_s[i]))), i
+    dev = torch.full((int(sizes.sum()),), -7, dtype=torch.int32, device="cuda")
+    eat.eat_query_batch_multi([c.net for c in nets], _dev(qs.net), _dev(qs.source), _dev(qs.t_s), dev,
+                              torch.as_tensor(offs).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), out)
