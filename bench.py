@@ -225,6 +225,90 @@ def run_ours_ragged(args):
     return 0
 
 
+def run_serve(args):
+    """Served queries: city network + 16 small grids resident; Poisson arrivals."""
+    import torch
+    import oracle
+    from paper_1912_00966_gb300 import eat
+
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    dev = torch.cuda.current_device()
+    tts = [synth.city()] + [synth.small_grid(seed_offset=k) for k in range(16)]
+    nets = [eat.eat_build(t.n_stops, t.u, t.v, t.dep, t.dur, device=dev,
+                          cluster_width=args.cluster_width) for t in tts]
+    scs = {}
+    results = []
+    for rate in args.serve_rates:
+        server = eat.Server(nets, max_batch=args.serve_batch, max_inflight=4,
+                            batch_wait_us=args.serve_wait_us)
+        rng = np.random.default_rng(rate)
+        n = int(rate * args.serve_seconds)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        qs = synth.random_queries(tts, n, 0x5E + rate)
+        pool = {j: [np.empty(tts[j].n_stops, np.int32) for _ in range(64)] for j in range(len(tts))}
+        inflight = {}
+        lat, lag, checked, bad = [], [], 0, 0
+        done = 0
+
+        def drain(timeout_us):
+            nonlocal done, checked, bad
+            for tag, status, net, l_ns in server.poll(timeout_us=timeout_us):
+                buf = inflight.pop(tag)
+                lat.append(l_ns / 1e6)
+                if status != 0:
+                    bad += 1
+                elif tag % 100 == 0:
+                    if net not in scs:
+                        scs[net] = oracle.SortedConnections(tts[net])
+                    want = oracle.csa(scs[net], int(qs.source[tag]), int(qs.t_s[tag]))
+                    checked += 1
+                    bad += int(not np.array_equal(buf, want))
+                pool[net].append(buf)
+                done += 1
+
+        t0 = time.perf_counter()
+        i = 0
+        while i < n:
+            now = time.perf_counter() - t0
+            while i < n and arrivals[i] <= now:
+                j = int(qs.net[i])
+                if not pool[j]:
+                    pool[j].append(np.empty(tts[j].n_stops, np.int32))
+                buf = pool[j].pop()
+                inflight[i] = buf
+                server.submit(j, int(qs.source[i]), int(qs.t_s[i]), buf, i)
+                lag.append((time.perf_counter() - t0 - arrivals[i]) * 1e3)
+                i += 1
+            drain(0)
+        while done < n:
+            drain(5000)
+        wall = time.perf_counter() - t0
+        st = server.stats()
+        server.close()
+        results.append({
+            "offered_qps": rate, "seconds": args.serve_seconds, "requests": n,
+            "sustained_qps": n / wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(np.max(lat)),
+            "submit_lag_p99_ms": float(np.percentile(lag, 99)),
+            "batches": st["batches"], "mean_batch": st["batched_queries"] / max(1, st["batches"]),
+            "max_inflight_batches": st["max_inflight_seen"], "checked_vs_oracle": checked,
+            "mismatches": bad,
+        })
+    line = {
+        "metric": "EAT serving latency and sustained queries/s", "unit": "ms / queries/s",
+        "n_gpus": 1, "higher_is_better": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "serve: city20k network + 16 grid1024 networks resident; "
+                               "Poisson arrivals, random network / source / t_s",
+                   "max_batch": args.serve_batch, "slots": 4,
+                   "batch_wait_us": args.serve_wait_us, "cluster_width_s": args.cluster_width},
+        "rates": results, "kernel_hash": kernel_hash(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def workload(name: str, seed_offset: int = 0):
     if name == "city":
         return synth.city(seed_offset=seed_offset), BATCH
@@ -568,7 +652,12 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="city", choices=["city", "small", "large", "ragged"])
+    ap.add_argument("--workload", default="city",
+                    choices=["city", "small", "large", "ragged", "serve"])
+    ap.add_argument("--serve-rates", type=int, nargs="+", default=[1000, 5000, 20000, 50000])
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-batch", type=int, default=256)
+    ap.add_argument("--serve-wait-us", type=int, default=200)
     ap.add_argument("--plain-queries", type=int, default=4096,
                     help="ragged workload: sequential single queries timed for comparison")
     ap.add_argument("--vwarp", type=int, default=0)
@@ -586,6 +675,8 @@ def main():
         return run_reference(args)
     if args.workload == "ragged":
         return run_ours_ragged(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -341,6 +341,65 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
 int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *times,
                        int32_t n, int32_t *out, void *stream);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop with continuous batching over resident networks (no
+ * counterpart in the paper, which runs one query at a time; each request runs
+ * the same algorithm as eat_query).  Requests for any of the server's networks
+ * are queued by eat_server_submit; a dispatcher thread keeps a pool of slots,
+ * each a CUDA stream with pre-allocated device buffers for max_batch queries.
+ * The pool size is set by mem_budget (admission by device memory: a request is
+ * admitted to the GPU only when a slot is free).  A free slot takes up to
+ * max_batch pending requests of any networks and runs them as one
+ * eat_query_batch_multi launch; batches started while others run overlap on
+ * the device.  When a batch finishes, each caller's row is written to its
+ * arr_out and a result (tag, status, latency) is queued for eat_server_poll.
+ * The networks must stay alive until eat_server_destroy. */
+typedef struct eat_server eat_server;
+
+typedef struct {
+    int32_t max_batch;      /* requests per launch; 0 = 256 */
+    int32_t max_inflight;   /* slots (concurrent launches); 0 = 4 */
+    int32_t batch_wait_us;  /* while another batch runs, wait up to this long for a
+                               fuller batch; 0 = 200 */
+    int32_t reserved;
+    int64_t mem_budget;     /* device + pinned bytes for the slots; 0 = 1 GiB */
+} eat_server_opts;
+
+typedef struct {
+    uint64_t tag;           /* the caller's tag from eat_server_submit */
+    int32_t status;         /* eat_status of the query */
+    int32_t net;            /* network index */
+    int64_t latency_ns;     /* submit to result delivered */
+} eat_server_result;
+
+typedef struct {
+    int64_t submitted, completed, pending;
+    int64_t batches, batched_queries;
+    int64_t max_batch_seen, max_inflight_seen, max_pending_seen;
+    int64_t slots, slot_bytes;
+    int64_t last_error;
+} eat_server_stats;
+
+/* Create a server for nets[0 .. n_nets-1] (same device, 1..EAT_MAX_NETS);
+ * opts may be NULL.  Errors: EAT_ERR_INVALID, EAT_ERR_NO_DEVICE, EAT_ERR_OOM
+ * (mem_budget holds no slot, or allocation failed). */
+int eat_server_create(const eat_net *const *nets, int32_t n_nets, const eat_server_opts *opts,
+                      eat_server **out);
+/* Queue query (s, t_s) on network `net`; arr_out (host memory, n_stops int32)
+ * receives the arrivals before the result is reported.  Never blocks on the GPU.
+ * Errors: EAT_ERR_INVALID (bad network or source, server shutting down). */
+int eat_server_submit(eat_server *sv, int32_t net, int32_t s, int32_t t_s, int32_t *arr_out,
+                      uint64_t tag);
+/* Move up to max finished results into results[], waiting up to timeout_us for
+ * the first one; returns how many were moved. */
+int32_t eat_server_poll(eat_server *sv, eat_server_result *results, int32_t max,
+                        int32_t timeout_us);
+/* Counters of the server since creation. */
+int eat_server_get_stats(eat_server *sv, eat_server_stats *out);
+/* Finish every queued request, then stop the dispatcher and free the slots.
+ * Results not yet polled are discarded.  NULL is ignored. */
+void eat_server_destroy(eat_server *sv);
+
 /*
  * eat_query_batch_noalloc -- eat_query_batch for callers that cannot allocate
  * device memory.  The paper has no counterpart; this entry point exists for

@@ -83,6 +83,23 @@ class eat_query_opts(ctypes.Structure):
                 ("status", _vp), ("counters", _vp)]
 
 
+class eat_server_opts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("batch_wait_us", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mem_budget", ctypes.c_int64)]
+
+
+class eat_server_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("net", ctypes.c_int32),
+                ("latency_ns", ctypes.c_int64)]
+
+
+class eat_server_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "submitted", "completed", "pending", "batches", "batched_queries", "max_batch_seen",
+        "max_inflight_seen", "max_pending_seen", "slots", "slot_bytes", "last_error")]
+
+
 def _sig(name, res, args):
     f = getattr(_lib, name)
     f.restype = res
@@ -111,7 +128,17 @@ _sig("eat_next_departure", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, _v
 _sig("eat_query_batch_noalloc", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp,
                                                ctypes.POINTER(eat_query_opts), _vp])
 
-EXPORTED = ("eat_last_error", "eat_version", "eat_build", "eat_build_csr", "eat_free", "eat_get_stats",
+_sig("eat_server_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32,
+                                         ctypes.POINTER(eat_server_opts), ctypes.POINTER(_vp)])
+_sig("eat_server_submit", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
+                                         ctypes.c_uint64])
+_sig("eat_server_poll", ctypes.c_int32, [_vp, ctypes.POINTER(eat_server_result), ctypes.c_int32,
+                                         ctypes.c_int32])
+_sig("eat_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(eat_server_stats)])
+_sig("eat_server_destroy", None, [_vp])
+
+EXPORTED = ("eat_server_create", "eat_server_submit", "eat_server_poll", "eat_server_get_stats",
+            "eat_server_destroy", "eat_last_error", "eat_version", "eat_build", "eat_build_csr", "eat_free", "eat_get_stats",
             "eat_net_host_view", "eat_query", "eat_workspace_bytes", "eat_query_batch",
             "eat_query_batch_multi", "eat_next_departure", "eat_query_batch_noalloc")
 
@@ -331,3 +358,44 @@ def eat_version() -> int:
 
 def eat_last_error() -> str:
     return _lib.eat_last_error().decode(errors="replace")
+
+
+class Server:
+    """Continuous-batching request loop over resident networks (eat_server_* in eat.h)."""
+
+    def __init__(self, nets, max_batch=0, max_inflight=0, batch_wait_us=0, mem_budget=0):
+        self._nets = list(nets)
+        arr = (_vp * len(self._nets))(*[x.handle.value for x in self._nets])
+        o = eat_server_opts(int(max_batch), int(max_inflight), int(batch_wait_us), 0,
+                            int(mem_budget))
+        h = _vp()
+        _check(_lib.eat_server_create(arr, len(self._nets), ctypes.byref(o), ctypes.byref(h)),
+               "eat_server_create")
+        self._h = h
+        self._buf = (eat_server_result * 4096)()
+
+    def submit(self, net, s, t_s, out, tag):
+        """Queue a query; `out` is a host int32 buffer of the network's n_stops (kept alive
+        by the caller until its result is polled)."""
+        _check(_lib.eat_server_submit(self._h, int(net), int(s), int(t_s), _ptr(out), int(tag)),
+               "eat_server_submit")
+
+    def poll(self, timeout_us=1000, max_results=4096):
+        n = _lib.eat_server_poll(self._h, self._buf, min(int(max_results), 4096), int(timeout_us))
+        return [(r.tag, r.status, r.net, r.latency_ns) for r in self._buf[:n]]
+
+    def stats(self):
+        st = eat_server_stats()
+        _check(_lib.eat_server_get_stats(self._h, ctypes.byref(st)), "eat_server_get_stats")
+        return {f: getattr(st, f) for f, _ in eat_server_stats._fields_}
+
+    def close(self):
+        if self._h:
+            _lib.eat_server_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
