@@ -341,6 +341,22 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
 int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *times,
                        int32_t n, int32_t *out, void *stream);
 
+/*
+ * eat_autotune -- choose the launch shape for this network by measurement (no
+ * counterpart in the paper, which fixes one thread per type or per edge and
+ * sweeps the virtual-warp size by hand, Section V-B).  Times every candidate
+ * block size (256, 512, 1024 threads) and vwarp (2, 4, 8, 16, 32 lanes per
+ * spilled stop) on the sample batch sources/times (n queries, device memory),
+ * each once to warm up and twice timed with CUDA events on `stream`, and stores
+ * the fastest for batches of about n queries in the network; afterwards every
+ * query call that leaves opts->block and opts->vwarp at 0 uses it.  The tuned
+ * shape is written to *best (may be NULL).  Blocks until done.  Allocates its
+ * own scratch (workspace and output rows) for the duration of the call.
+ * Errors: as eat_query_batch.
+ */
+int eat_autotune(eat_net *net, const int32_t *sources, const int32_t *times, int32_t n,
+                 eat_query_opts *best, void *stream);
+
 /* ------------------------------------------------------------------ serving
  * A request loop with continuous batching over resident networks (no
  * counterpart in the paper, which runs one query at a time; each request runs

@@ -116,17 +116,24 @@ static constexpr size_t kWsHeader = 256;   // work counter + internal status / c
 static constexpr size_t kQueueEntryBytes = 16;  // (stop, type) item x 2 buffers
 
 static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_query_opts *o,
-                     Plan &p, int32_t vmin = -1) {
+                     Plan &p, int32_t vmin = -1, const eat_net *tuned = nullptr) {
     if (vmin < 0) vmin = vmax;
     DeviceInfo d;
     int rc = device_info(dev, d);
     if (rc) return rc;
     p.nets = n_nets == 1 ? 1 : EAT_MAX_NETS;
     p.vmax = vmax;
-    p.block = (o && o->block) ? o->block : 512;
+    int tb = 0, tv = 0;
+    if (tuned && n > 0) {
+        int cls = 0;
+        while (cls < 31 && (1 << (cls + 1)) <= n) ++cls;
+        tb = tuned->tuned_block[cls];
+        tv = tuned->tuned_vwarp[cls];
+    }
+    p.block = (o && o->block) ? o->block : (tb ? tb : 512);
     if (p.block < 64 || p.block > 1024 || p.block % 32)
         return fail(EAT_ERR_INVALID, "block must be a multiple of 32 in 64..1024");
-    int vw = (o && o->vwarp) ? o->vwarp : 8;
+    int vw = (o && o->vwarp) ? o->vwarp : (tv ? tv : 8);
     int l = 0;
     while ((1 << l) < vw) ++l;
     if ((1 << l) != vw || vw > 32) return fail(EAT_ERR_INVALID, "vwarp must be 1, 2, 4, 8, 16 or 32");
@@ -261,7 +268,7 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
         vmin = std::min(vmin, nets[i]->host.n_stops);
     }
     Plan p;
-    int rc = make_plan(dev, vmax, n, n_nets, o, p, vmin);
+    int rc = make_plan(dev, vmax, n, n_nets, o, p, vmin, n_nets == 1 ? nets[0] : nullptr);
     if (rc) return rc;
     if (ws_bytes < p.ws_bytes)
         return fail(EAT_ERR_WORKSPACE, "workspace of " + std::to_string(ws_bytes) +
@@ -473,7 +480,8 @@ size_t eat_workspace_bytes(const eat_net *const *nets, int32_t n_nets, int32_t n
         vmin = std::min(vmin, nets[i]->host.n_stops);
     }
     Plan p;
-    if (make_plan(nets[0]->device, vmax, n, n_nets, opts, p, vmin)) return 0;
+    if (make_plan(nets[0]->device, vmax, n, n_nets, opts, p, vmin, n_nets == 1 ? nets[0] : nullptr))
+        return 0;
     return p.ws_bytes;
 }
 
@@ -485,7 +493,7 @@ int eat_query(const eat_net *net, int32_t s, int32_t t_s, int32_t *arr_out,
     if (s < 0 || s >= net->host.n_stops) return fail(EAT_ERR_INVALID, "source out of range");
     std::lock_guard<std::mutex> g(net->ws_lock);
     Plan p;
-    int rc = make_plan(net->device, net->host.n_stops, 1, 1, nullptr, p);
+    int rc = make_plan(net->device, net->host.n_stops, 1, 1, nullptr, p, -1, net);
     if (rc) return rc;
     DeviceGuard guard(net->device);
     const bool dev_out = is_device_ptr(arr_out);
@@ -678,6 +686,85 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
 
 }  // extern "C"
 
+// ------------------------------------------------------------------ autotuning
+
+extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t *times,
+                            int32_t n, eat_query_opts *best, void *stream) {
+    clear_error();
+    if (!net) return fail(EAT_ERR_INVALID, "NULL network");
+    if (net->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
+    if (n <= 0 || !sources || !times) return fail(EAT_ERR_INVALID, "empty sample");
+    DeviceGuard guard(net->device);
+    if (!is_device_ptr(sources) || !is_device_ptr(times))
+        return fail(EAT_ERR_INVALID, "sample arrays must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    const eat_net *nets[1] = {net};
+    size_t ws_need = 0;
+    for (int b : {256, 512, 1024}) {
+        eat_query_opts o{};
+        o.block = b;
+        o.vwarp = 8;
+        ws_need = std::max(ws_need, eat_workspace_bytes(nets, 1, n, &o));
+    }
+    if (!ws_need) return EAT_ERR_INVALID;
+    void *ws = nullptr, *rows = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&ws, ws_need);
+    if (e == cudaSuccess) e = cudaMalloc(&rows, (size_t)n * (size_t)net->host.n_stops * 4);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int rc = EAT_OK;
+    int best_b = 512, best_v = 8;
+    float best_ms = 1e30f;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(EAT_ERR_OOM, std::string("autotune scratch: ") + cudaGetErrorString(e));
+    }
+    for (int b : {256, 512, 1024}) {
+        for (int v : {2, 4, 8, 16, 32}) {
+            if (rc) break;
+            eat_query_opts o{};
+            o.block = b;
+            o.vwarp = v;
+            float total = 0.f;
+            for (int rep = 0; rep < 3 && !rc; ++rep) {
+                if (rep > 0) cudaEventRecord(e0, st);
+                rc = run_batch(nets, 1, nullptr, sources, times, n, (int32_t *)rows, nullptr, ws,
+                               ws_need, &o, st, nullptr, nullptr);
+                if (rc) break;
+                if (rep > 0) {
+                    cudaEventRecord(e1, st);
+                    e = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
+                    total += ms;
+                }
+            }
+            if (!rc && total < best_ms) {
+                best_ms = total;
+                best_b = b;
+                best_v = v;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ws) cudaFree(ws);
+    if (rows) cudaFree(rows);
+    if (rc) return rc;
+    int cls = 0;
+    while (cls < 31 && (1 << (cls + 1)) <= n) ++cls;
+    net->tuned_block[cls] = best_b;
+    net->tuned_vwarp[cls] = best_v;
+    if (best) {
+        *best = eat_query_opts{};
+        best->block = best_b;
+        best->vwarp = best_v;
+    }
+    return EAT_OK;
+}
+
 // ------------------------------------------------------------------ no-allocation entry point
 
 // Fixed scratch for eat_query_batch_noalloc: the work counter (first 256 bytes)
@@ -724,7 +811,7 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     if (!is_device_ptr(sources) || !is_device_ptr(times) || !is_device_ptr(arr_out))
         return fail(EAT_ERR_INVALID, "sources, times and arr_out must be device memory");
     Plan p;
-    int rc = make_plan(net->device, net->host.n_stops, n, 1, opts, p);
+    int rc = make_plan(net->device, net->host.n_stops, n, 1, opts, p, -1, net);
     if (rc) return rc;
     // Fewer persistent blocks so that their queue spill fits the fixed scratch.
     const size_t per_block = (size_t)p.spill_stride * 4 + (size_t)p.mask_stride * 4;

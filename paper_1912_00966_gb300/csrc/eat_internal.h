@@ -80,6 +80,9 @@ struct eat_net {
     mutable size_t ws_bytes = 0;
     mutable void *stage = nullptr;
     mutable size_t stage_bytes = 0;
+    // Launch shapes chosen by eat_autotune, per batch-size class (log2 of n).
+    mutable int32_t tuned_block[32] = {0};
+    mutable int32_t tuned_vwarp[32] = {0};
 };
 
 namespace eat {

@@ -128,6 +128,7 @@ _sig("eat_next_departure", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, _v
 _sig("eat_query_batch_noalloc", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp,
                                                ctypes.POINTER(eat_query_opts), _vp])
 
+_sig("eat_autotune", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.POINTER(eat_query_opts), _vp])
 _sig("eat_server_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32,
                                          ctypes.POINTER(eat_server_opts), ctypes.POINTER(_vp)])
 _sig("eat_server_submit", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
@@ -137,7 +138,7 @@ _sig("eat_server_poll", ctypes.c_int32, [_vp, ctypes.POINTER(eat_server_result),
 _sig("eat_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(eat_server_stats)])
 _sig("eat_server_destroy", None, [_vp])
 
-EXPORTED = ("eat_server_create", "eat_server_submit", "eat_server_poll", "eat_server_get_stats",
+EXPORTED = ("eat_autotune", "eat_server_create", "eat_server_submit", "eat_server_poll", "eat_server_get_stats",
             "eat_server_destroy", "eat_last_error", "eat_version", "eat_build", "eat_build_csr", "eat_free", "eat_get_stats",
             "eat_net_host_view", "eat_query", "eat_workspace_bytes", "eat_query_batch",
             "eat_query_batch_multi", "eat_next_departure", "eat_query_batch_noalloc")
@@ -343,6 +344,15 @@ def eat_query_batch_noalloc(net: Net, sources, times, out, stream=None, **opts):
                                         int(sources.shape[0]), _ptr(out), ctypes.byref(o),
                                         _stream_handle(stream)), "eat_query_batch_noalloc")
     return out
+
+
+def eat_autotune(net: Net, sources, times, stream=None) -> dict:
+    """Time the candidate launch shapes on a sample batch (device int32 arrays) and keep the
+    fastest for this network and batch size; returns {"block": b, "vwarp": v}."""
+    o = eat_query_opts()
+    _check(_lib.eat_autotune(net.handle, _ptr(sources), _ptr(times), int(sources.shape[0]),
+                             ctypes.byref(o), _stream_handle(stream)), "eat_autotune")
+    return {"block": o.block, "vwarp": o.vwarp}
 
 
 def eat_next_departure(net: Net, types, times, out, stream=None):
