@@ -494,7 +494,13 @@ def run_ours(args):
     out = torch.empty(batch * V, dtype=torch.int32, device="cuda")
     cnt = torch.zeros((n_steps, batch, 7), dtype=torch.int64, device="cuda")
     status = torch.zeros((n_steps, batch), dtype=torch.int32, device="cuda")
-    opts = dict(vwarp=args.vwarp, block=args.block)
+    opts = dict(vwarp=args.vwarp, block=args.block, mode=args.mode)
+    tuned = None
+    if args.autotune and not (args.vwarp or args.block or args.mode):
+        # Launch shape chosen by the library's autotuner on a sample batch (setup, untimed).
+        sample = synth.random_queries(tt, batch, 0xB0 - 1)
+        tuned = eat.eat_autotune(net, torch.as_tensor(sample.source).cuda(),
+                                 torch.as_tensor(sample.t_s).cuda())
     ws = torch.empty(eat.eat_workspace_bytes(net, batch, **opts), dtype=torch.uint8, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -628,6 +634,8 @@ def run_ours(args):
         "connections_relaxed_per_s": tot["types"] / (gpu_s / world),
         "subtrips": {0: "none", 1: "sqrt(k) per trip", 2: "sqrt(mean trip length)"}[args.subtrips],
         "cluster_width_s": args.cluster_width,
+        "launch_shape": tuned if tuned else {"block": args.block, "vwarp": args.vwarp,
+                                             "mode": args.mode},
         "without_subtrips": None if base_ms is None else
             {"value": batch / (base_ms / 1e3), "unit": "queries/s", "ms_per_step": base_ms},
         "build_s": t_build,
@@ -660,6 +668,8 @@ def main():
                     help="ragged workload: sequential single queries timed for comparison")
     ap.add_argument("--vwarp", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--mode", type=int, default=0, help="0 auto, 1 rounds, 3 asynchronous")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--cluster-width", type=int, default=1800,
                     help="seconds per departure cluster (Section III-D uses one hour; Section V-B finds narrower clusters faster)")

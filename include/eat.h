@@ -179,7 +179,11 @@ enum eat_placement {
 enum eat_mode {
     EAT_MODE_AUTO = 0,  /* library picks */
     EAT_MODE_CTA = 1,   /* one thread block per query; rounds end at block barriers */
-    EAT_MODE_GRID = 2   /* all SMs on each round of one query at a time */
+    EAT_MODE_GRID = 2,  /* reserved: all SMs on each round of one query (not available) */
+    EAT_MODE_ASYNC = 3  /* one thread block per query, no rounds: warps claim pending stops
+                           from a bitmap and relax their types as soon as they appear;
+                           needs the bitmap (n_stops bits) in shared memory; the round cap
+                           does not apply and counters.rounds is 0 */
 };
 
 /* Error message of the calling thread's last failed call ("" if none). */
@@ -345,11 +349,13 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
  * eat_autotune -- choose the launch shape for this network by measurement (no
  * counterpart in the paper, which fixes one thread per type or per edge and
  * sweeps the virtual-warp size by hand, Section V-B).  Times every candidate
- * block size (256, 512, 1024 threads) and vwarp (2, 4, 8, 16, 32 lanes per
- * spilled stop) on the sample batch sources/times (n queries, device memory),
- * each once to warm up and twice timed with CUDA events on `stream`, and stores
- * the fastest for batches of about n queries in the network; afterwards every
- * query call that leaves opts->block and opts->vwarp at 0 uses it.  The tuned
+ * block size (256, 512, 1024 threads) with the round-based mode and every vwarp
+ * (2, 4, 8, 16, 32 lanes per spilled stop), and with the asynchronous mode, on
+ * the sample batch sources/times (n queries, device memory), each once to warm
+ * up and twice timed with CUDA events on `stream`, and stores the fastest for
+ * batches of about n queries in the network; afterwards every query call that
+ * leaves opts->block, opts->vwarp and opts->mode at 0 uses it (a call with a
+ * round cap keeps the round-based mode).  The tuned
  * shape is written to *best (may be NULL).  Blocks until done.  Allocates its
  * own scratch (workspace and output rows) for the duration of the call.
  * Errors: as eat_query_batch.

@@ -80,12 +80,12 @@ static int device_info(int dev, DeviceInfo &out) {
         // Allow every CTA kernel the full opt-in shared memory (once per device).
         DeviceGuard guard(dev);
         for (int nets : {1, EAT_MAX_NETS})
-            for (int mem = 0; mem < 4; ++mem) {
-                e = cudaFuncSetAttribute(cta_kernel(nets, mem),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(d.smem_optin - d.reserve));
-                if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-            }
+            for (int mem = 0; mem < 4; ++mem)
+                for (const void *k : {cta_kernel(nets, mem), async_kernel(nets, mem)}) {
+                    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(d.smem_optin - d.reserve));
+                    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+                }
         d.init = true;
     }
     out = d;
@@ -110,10 +110,62 @@ struct Plan {
     size_t ws_bytes = 0;
     size_t off_spill = 0, off_mask = 0;
     int nets = 1;
+    bool async = false;           // round-free kernel (EAT_MODE_ASYNC)
 };
 
 static constexpr size_t kWsHeader = 256;   // work counter + internal status / counters
 static constexpr size_t kQueueEntryBytes = 16;  // (stop, type) item x 2 buffers
+
+// Plan of the round-free kernel: arrivals (shared when they fit), one bitmap and
+// a 512-byte staging area per warp in shared memory; no spill queues.
+static int make_async_plan(int dev, const DeviceInfo &d, int32_t vmax, int32_t n, int n_nets,
+                           const eat_query_opts *o, Plan &p, int32_t vmin) {
+    p.async = true;
+    const size_t words = ((size_t)vmax + 31) / 32;
+    p.mask_words = (int32_t)align_up(words, 4);
+    const size_t arr_bytes = align_up((size_t)vmax, 4) * 4;
+    const size_t stage_bytes = (size_t)(p.block / 32) * 128 * 4;
+    const size_t limit = d.smem_optin - d.reserve;
+    const size_t half = d.smem_per_sm / 2 - d.reserve;
+    const int place = o ? o->placement : EAT_PLACE_AUTO;
+    const size_t fixed = (size_t)p.mask_words * 4 + stage_bytes;
+    if (fixed > limit) return fail(EAT_ERR_INVALID, "bitmap does not fit in shared memory");
+    p.smem_arr_cap = 0;
+    if (place == EAT_PLACE_GLOBAL) return fail(EAT_ERR_INVALID, "asynchronous mode keeps the bitmap in shared memory");
+    if (place == EAT_PLACE_SHARED) {
+        if (arr_bytes + fixed > limit) return fail(EAT_ERR_INVALID, "arrivals do not fit in shared memory");
+        p.mem = 0;
+    } else if (place == EAT_PLACE_GLOBAL_ARR) {
+        p.mem = 1;
+    } else if (arr_bytes + fixed <= half || (n_nets == 1 && arr_bytes + fixed <= limit)) {
+        p.mem = 0;
+    } else if (vmin < vmax && fixed + (size_t)vmin * 4 <= half) {
+        p.mem = 3;
+        p.smem_arr_cap = (int32_t)std::min<size_t>((half - fixed) / 4 & ~(size_t)3, (size_t)vmax);
+    } else {
+        p.mem = 1;
+    }
+    p.smem_mask_off = p.mem == 0 ? (int32_t)(arr_bytes / 4) : p.mem == 3 ? p.smem_arr_cap : 0;
+    p.smem_q_off = p.smem_mask_off + p.mask_words;
+    p.smem = (size_t)p.smem_q_off * 4 + stage_bytes;
+    p.qcap = 0;
+    int per_sm = 0;
+    cudaError_t e;
+    {
+        DeviceGuard guard(dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, async_kernel(p.nets, p.mem),
+                                                          p.block, p.smem);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) return fail(EAT_ERR_INVALID, "kernel does not fit on an SM with this block size");
+    p.grid = (int)std::min<int64_t>((int64_t)std::max(n, 1), (int64_t)per_sm * d.sms);
+    p.spill_stride = 0;
+    p.mask_stride = 0;
+    p.off_spill = kWsHeader;
+    p.off_mask = kWsHeader;
+    p.ws_bytes = kWsHeader;
+    return EAT_OK;
+}
 
 static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_query_opts *o,
                      Plan &p, int32_t vmin = -1, const eat_net *tuned = nullptr) {
@@ -123,12 +175,13 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     if (rc) return rc;
     p.nets = n_nets == 1 ? 1 : EAT_MAX_NETS;
     p.vmax = vmax;
-    int tb = 0, tv = 0;
+    int tb = 0, tv = 0, tm = 0;
     if (tuned && n > 0) {
         int cls = 0;
         while (cls < 31 && (1 << (cls + 1)) <= n) ++cls;
         tb = tuned->tuned_block[cls];
         tv = tuned->tuned_vwarp[cls];
+        tm = tuned->tuned_mode[cls];
     }
     p.block = (o && o->block) ? o->block : (tb ? tb : 512);
     if (p.block < 64 || p.block > 1024 || p.block % 32)
@@ -138,8 +191,12 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     while ((1 << l) < vw) ++l;
     if ((1 << l) != vw || vw > 32) return fail(EAT_ERR_INVALID, "vwarp must be 1, 2, 4, 8, 16 or 32");
     p.vw_log2 = l;
-    if (o && o->mode != EAT_MODE_AUTO && o->mode != EAT_MODE_CTA)
-        return fail(EAT_ERR_INVALID, "mode must be EAT_MODE_AUTO or EAT_MODE_CTA");
+    if (o && o->mode != EAT_MODE_AUTO && o->mode != EAT_MODE_CTA && o->mode != EAT_MODE_ASYNC)
+        return fail(EAT_ERR_INVALID, "mode must be EAT_MODE_AUTO, EAT_MODE_CTA or EAT_MODE_ASYNC");
+    const bool rounds_needed = o && o->max_rounds > 0;   // the round cap needs rounds
+    if ((o && o->mode == EAT_MODE_ASYNC) ||
+        (tm == EAT_MODE_ASYNC && !rounds_needed && (!o || o->mode == EAT_MODE_AUTO)))
+        return make_async_plan(dev, d, vmax, n, n_nets, o, p, vmin);
     const int place = o ? o->placement : EAT_PLACE_AUTO;
     if (place < EAT_PLACE_AUTO || place > EAT_PLACE_GLOBAL)
         return fail(EAT_ERR_INVALID, "placement must be one of EAT_PLACE_*");
@@ -190,7 +247,7 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     }
     p.smem_mask_off = p.mem == 0 ? (int32_t)(arr_bytes / 4) : p.mem == 3 ? p.smem_arr_cap : 0;
     p.smem_q_off = p.smem_mask_off + (p.mem != 2 ? 2 * p.mask_words : 0);
-    p.smem = (size_t)p.smem_q_off * 4 + kQueueEntryBytes * (size_t)p.qcap;
+    p.smem = b0 + kQueueEntryBytes * (size_t)p.qcap;
 
     int per_sm = 0;
     cudaError_t e;
@@ -283,8 +340,9 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     NetDev devs[EAT_MAX_NETS];
     for (int i = 0; i < n_nets; ++i) devs[i] = nets[i]->dev;
-    e = launch_cta(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st);
-    if (e != cudaSuccess) return cuda_fail(e, "CTA kernel launch");
+    e = p.async ? launch_async(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st)
+                : launch_cta(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "query kernel launch");
     return EAT_OK;
 }
 
@@ -704,6 +762,7 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
         eat_query_opts o{};
         o.block = b;
         o.vwarp = 8;
+        o.mode = EAT_MODE_CTA;
         ws_need = std::max(ws_need, eat_workspace_bytes(nets, 1, n, &o));
     }
     if (!ws_need) return EAT_ERR_INVALID;
@@ -720,12 +779,25 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
         cudaGetLastError();
         rc = fail(EAT_ERR_OOM, std::string("autotune scratch: ") + cudaGetErrorString(e));
     }
+    int best_m = EAT_MODE_CTA;
+    struct Cand { int m, b, v; };
+    std::vector<Cand> cands;
     for (int b : {256, 512, 1024}) {
-        for (int v : {2, 4, 8, 16, 32}) {
+        for (int v : {2, 4, 8, 16, 32}) cands.push_back({EAT_MODE_CTA, b, v});
+        cands.push_back({EAT_MODE_ASYNC, b, 8});
+    }
+    for (const Cand &cd : cands) {
+        {
+            const int b = cd.b, v = cd.v;
             if (rc) break;
             eat_query_opts o{};
             o.block = b;
             o.vwarp = v;
+            o.mode = cd.m;
+            if (cd.m == EAT_MODE_ASYNC && !eat_workspace_bytes(nets, 1, n, &o)) {
+                clear_error();
+                continue;                      // bitmap does not fit: not a candidate
+            }
             float total = 0.f;
             for (int rep = 0; rep < 3 && !rc; ++rep) {
                 if (rep > 0) cudaEventRecord(e0, st);
@@ -745,6 +817,7 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
                 best_ms = total;
                 best_b = b;
                 best_v = v;
+                best_m = cd.m;
             }
         }
     }
@@ -757,10 +830,12 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
     while (cls < 31 && (1 << (cls + 1)) <= n) ++cls;
     net->tuned_block[cls] = best_b;
     net->tuned_vwarp[cls] = best_v;
+    net->tuned_mode[cls] = best_m;
     if (best) {
         *best = eat_query_opts{};
         best->block = best_b;
         best->vwarp = best_v;
+        best->mode = best_m;
     }
     return EAT_OK;
 }
@@ -815,7 +890,7 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     if (rc) return rc;
     // Fewer persistent blocks so that their queue spill fits the fixed scratch.
     const size_t per_block = (size_t)p.spill_stride * 4 + (size_t)p.mask_stride * 4;
-    const size_t fit = (EAT_NOALLOC_SCRATCH_BYTES - kWsHeader) / per_block;
+    const size_t fit = per_block ? (EAT_NOALLOC_SCRATCH_BYTES - kWsHeader) / per_block : (size_t)p.grid;
     if (fit < 1)
         return fail(EAT_ERR_INVALID, "network too large for the no-allocation scratch");
     const int grid = (int)std::min<size_t>((size_t)p.grid, fit);
@@ -830,7 +905,8 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     // The query counter must start at zero; the queues need no clearing.
     cudaError_t e = cudaMemsetAsync(qa.work, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-allocation scratch)");
-    e = launch_cta(&net->dev, 1, qa, p.mem, grid, p.block, p.smem, st);
-    if (e != cudaSuccess) return cuda_fail(e, "CTA kernel launch");
+    e = p.async ? launch_async(&net->dev, 1, qa, p.mem, grid, p.block, p.smem, st)
+                : launch_cta(&net->dev, 1, qa, p.mem, grid, p.block, p.smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "query kernel launch");
     return EAT_OK;
 }

@@ -83,6 +83,7 @@ struct eat_net {
     // Launch shapes chosen by eat_autotune, per batch-size class (log2 of n).
     mutable int32_t tuned_block[32] = {0};
     mutable int32_t tuned_vwarp[32] = {0};
+    mutable int32_t tuned_mode[32] = {0};
 };
 
 namespace eat {

@@ -119,13 +119,23 @@ __device__ __forceinline__ int32_t cluster_slot(const NetDev &N, int32_t e) {
     return k < 0 ? 0 : k;
 }
 
+// One 32-byte cluster entry in a single 256-bit load (sm_100 and later), read
+// through the non-coherent path: the entries never change during a query.
+__device__ __forceinline__ void load_entry(const int4 *c, int4 &a, int4 &b) {
+    asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+        : "l"(c));
+}
+
 // getConnection of type t at time e: least departure >= e, or kInf.
 __device__ __forceinline__ int32_t next_departure(const NetDev &N, int32_t t, int32_t e,
                                                   int32_t &aps) {
     const int32_t k = cluster_slot(N, e);
     if (k >= N.y) return kInf;
     const int4 *c = N.ce + 2 * ((int64_t)t * N.y + k);
-    return cluster_lookup(__ldg(c), __ldg(c + 1), e, N.apx, aps);
+    int4 a, b;
+    load_entry(c, a, b);
+    return cluster_lookup(a, b, e, N.apx, aps);
 }
 
 enum { kArrGlobal = 0, kArrShared = 1, kArrPerQuery = 2 };
@@ -232,7 +242,9 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                 ++c_lookups;
                 const int4 ty = __ldg(N.ty + t);            // {v, lambda, row of v}
                 const int4 *c = N.ce + 2 * ((int64_t)t * N.y + k);
-                const int32_t tc = cluster_lookup(__ldg(c), __ldg(c + 1), e_u, N.apx, c_aps);
+                int4 ca, cb;
+                load_entry(c, ca, cb);
+                const int32_t tc = cluster_lookup(ca, cb, e_u, N.apx, c_aps);
                 if (tc == kInf) return;                     // no departure left (Section IV-D)
                 ++c_evals;
                 const int32_t v = ty.x;
@@ -335,6 +347,206 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
     }
 }
 
+// ------------------------------------------------------------------ asynchronous mode
+//
+// The same fixpoint without rounds.  The frontier is a bitmap of pending stops in
+// shared memory.  Each warp works on its own: it reads 32 bitmap words (one per
+// lane), every lane claims one pending stop (clears its bit, then reads e[u]), the
+// warp spreads the claimed stops' (stop, type) pairs over its lanes and relaxes
+// them; a lowered e[v] sets v's bit after the atomicMin, so a stop improved after
+// it was read is claimed again (the invariant of Section IV-B's double buffer,
+// without the round barrier).  A work counter holds pending + claimed stops:
+// a producer adds one before publishing a bit, a claimed stop is subtracted only
+// after all its pushes, so the counter reaches zero exactly when no work is left.
+// Every idle wait is capped; hitting the cap reports EAT_ERR_NO_CONVERGENCE.
+
+constexpr int32_t kIdleCap = 1 << 24;       // empty chunk scans in a row before giving up
+
+template <int NETS, int ARR>
+__global__ void __launch_bounds__(1024, 1)
+eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) {
+    extern __shared__ __align__(16) int32_t smem[];
+    __shared__ int32_t s_q;
+    __shared__ int32_t s_work;
+    __shared__ int32_t s_err;
+    __shared__ unsigned long long s_cnt[6];
+
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nwarps = nthr >> 5;
+    uint32_t *const mask = (uint32_t *)(smem + qa.smem_mask_off);
+    // Per-warp staging of claimed stops: row begin, exclusive item prefix, e[u], cluster.
+    int32_t *const stage = smem + qa.smem_q_off + warp * (4 * 32);
+    int32_t *const st_beg = stage, *const st_pre = stage + 32, *const st_e = stage + 64,
+                   *const st_k = stage + 96;
+
+    for (;;) {
+        if (tid == 0) s_q = atomicAdd(qa.work, 1);
+        if (tid < 6) s_cnt[tid] = 0;
+        __syncthreads();
+        const int q = s_q;
+        if (q >= qa.n) break;
+
+        const int ni = (NETS == 1 || qa.net_idx == nullptr) ? 0 : __ldg(qa.net_idx + q);
+        const bool net_ok = (unsigned)ni < (unsigned)qa.n_nets;
+        const NetDev &N = nets.net[net_ok ? ni : 0];
+        const int32_t V = N.n_stops;
+        const int64_t off = qa.arr_off ? __ldg(qa.arr_off + q) : (int64_t)q * V;
+        int32_t *const out = qa.arr_out + off;
+        const bool arr_shared = ARR == kArrShared || (ARR == kArrPerQuery && V <= qa.smem_arr_cap);
+        int32_t *const arr = arr_shared ? smem : out;
+        const int32_t nwords = (V + 31) >> 5;
+        const int32_t nchunks = (nwords + 31) >> 5;
+
+        for (int32_t i = tid; i < V; i += nthr) arr[i] = kInf;
+        for (int32_t i = tid; i < nwords; i += nthr) mask[i] = 0u;
+        if (tid == 0) {
+            s_work = 0;
+            s_err = 0;
+        }
+        const int32_t s = __ldg(qa.src + q);
+        const int32_t t_s = __ldg(qa.ts + q);
+        const bool valid = net_ok && (unsigned)s < (unsigned)V;
+        __syncthreads();
+        if (tid == 0 && valid) {
+            arr[s] = t_s;
+            mask[s >> 5] = 1u << (s & 31);
+            s_work = 1;
+        }
+        __syncthreads();
+
+        int32_t c_vert = 0, c_types = 0, c_evals = 0, c_lookups = 0, c_aps = 0, c_relax = 0;
+        int32_t chunk = nchunks > 0 ? warp % nchunks : 0;
+        int32_t idle = 0, passes = 0;
+        bool go = valid;
+        while (go) {
+            // Claim up to one pending stop per lane from this chunk's 32 words.
+            const int32_t word = chunk * 32 + lane;
+            int32_t u = -1;
+            if (word < nwords) {
+                const uint32_t w = *((volatile uint32_t *)mask + word);
+                if (w) {
+                    const uint32_t bit = w & (0u - w);
+                    if (atomicAnd(mask + word, ~bit) & bit) u = word * 32 + (__ffs(w) - 1);
+                }
+            }
+            const uint32_t claimed = __ballot_sync(0xffffffffu, u >= 0);
+            if (claimed == 0) {
+                chunk = chunk + 1 == nchunks ? 0 : chunk + 1;
+                ++passes;                         // empty chunk scans in a row
+                if (++idle >= nchunks) {          // a full pass found nothing
+                    idle = 0;
+                    int32_t stop = 0;
+                    if (lane == 0) {
+                        const int32_t wk = *((volatile int32_t *)&s_work);
+                        const int32_t er = *((volatile int32_t *)&s_err);
+                        stop = (wk == 0 || er) ? 1 : (passes > kIdleCap ? 2 : 0);
+                        if (stop == 2) atomicExch(&s_err, 1);
+                    }
+                    stop = __shfl_sync(0xffffffffu, stop, 0);
+                    if (stop) break;
+                    __nanosleep(200);
+                }
+                continue;
+            }
+            idle = 0;
+            passes = 0;
+            // Expand the claimed stops: read e[u] after the claim (fence), then the row.
+            __threadfence_block();
+            int32_t d = 0, beg = 0, e_u = 0, k = 0;
+            if (u >= 0) {
+                ++c_vert;
+                e_u = load_arr(arr, u, arr_shared);
+                k = cluster_slot(N, e_u);
+                beg = __ldg(N.row_ptr + u);
+                const int32_t end = __ldg(N.row_ptr + u + 1);
+                if (k < N.y) d = end - beg;
+                else c_types += end - beg;
+            }
+            int32_t incl = d;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            st_beg[lane] = beg;
+            st_pre[lane] = incl - d;
+            st_e[lane] = e_u;
+            st_k[lane] = k;
+            __syncwarp();
+            for (int32_t j = lane; j < total; j += 32) {
+                // owner: the last lane whose exclusive prefix is <= j (lanes without
+                // items share the next lane's prefix and sit before it)
+                int32_t lo = 0, hi = 31;
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi + 1) >> 1;
+                    if (st_pre[mid] <= j) lo = mid; else hi = mid - 1;
+                }
+                const int32_t t = st_beg[lo] + (j - st_pre[lo]);
+                const int32_t eu = st_e[lo], kk = st_k[lo];
+                ++c_types;
+                ++c_lookups;
+                const int4 ty = __ldg(N.ty + t);             // {v, lambda, row of v}
+                const int4 *c = N.ce + 2 * ((int64_t)t * N.y + kk);
+                int4 ca, cb;
+                load_entry(c, ca, cb);
+                const int32_t tc = cluster_lookup(ca, cb, eu, N.apx, c_aps);
+                if (tc == kInf) continue;
+                ++c_evals;
+                const int32_t v = ty.x;
+                const int32_t cand = tc + ty.y;
+                if (cand >= load_arr(arr, v, arr_shared)) continue;
+                const int32_t old = atomicMin(arr + v, cand);
+                if (cand >= old) continue;
+                ++c_relax;
+                if (ty.w - ty.z <= 0) continue;            // v has no outgoing types
+                const uint32_t bit = 1u << (v & 31);
+                atomicAdd(&s_work, 1);                      // count before publishing
+                __threadfence_block();
+                if (atomicOr(mask + (v >> 5), bit) & bit) atomicAdd(&s_work, -1);
+            }
+            __syncwarp();
+            // The claimed stops are done once all their pushes are published.
+            __threadfence_block();
+            if (lane == 0) atomicAdd(&s_work, -__popc(claimed));
+        }
+        __syncthreads();
+
+        if (arr_shared)
+            for (int32_t i = tid; i < V; i += nthr) out[i] = arr[i];
+        if (tid == 0 && qa.status)
+            qa.status[q] = !valid ? EAT_ERR_INVALID : (s_err ? EAT_ERR_NO_CONVERGENCE : EAT_OK);
+        if (qa.counters) {
+            unsigned long long c[6] = {(unsigned long long)c_vert, (unsigned long long)c_types,
+                                       (unsigned long long)c_evals, (unsigned long long)c_lookups,
+                                       (unsigned long long)c_aps, (unsigned long long)c_relax};
+#pragma unroll
+            for (int j = 0; j < 6; ++j)
+                for (int o = 16; o > 0; o >>= 1) c[j] += __shfl_down_sync(0xffffffffu, c[j], o);
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) atomicAdd(&s_cnt[j], c[j]);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                eat_counters r;
+                r.rounds = 0;                       // no rounds in this mode
+                r.vertices = (int64_t)s_cnt[0];
+                r.types = (int64_t)s_cnt[1];
+                r.evals = (int64_t)s_cnt[2];
+                r.lookups = (int64_t)s_cnt[3];
+                r.aps = (int64_t)s_cnt[4];
+                r.relaxed = (int64_t)s_cnt[5];
+                qa.counters[q] = r;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void eat_next_departure_kernel(const NetDev N, const int32_t *types,
                                           const int32_t *times, int32_t n, int32_t *out) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,6 +570,39 @@ static const void *cta_kernel_ptr(int mem) {
 
 const void *cta_kernel(int nets, int mem) {
     return nets == 1 ? cta_kernel_ptr<1>(mem) : cta_kernel_ptr<EAT_MAX_NETS>(mem);
+}
+
+template <int NETS>
+static const void *async_kernel_ptr(int mem) {
+    switch (mem) {
+    case 0: return (const void *)eat_async_kernel<NETS, kArrShared>;
+    case 3: return (const void *)eat_async_kernel<NETS, kArrPerQuery>;
+    default: return (const void *)eat_async_kernel<NETS, kArrGlobal>;
+    }
+}
+
+const void *async_kernel(int nets, int mem) {
+    return nets == 1 ? async_kernel_ptr<1>(mem) : async_kernel_ptr<EAT_MAX_NETS>(mem);
+}
+
+template <int NETS>
+static cudaError_t launch_async_t(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem,
+                                  int grid, int block, size_t smem, cudaStream_t st) {
+    NetTable<NETS> tab;
+    for (int i = 0; i < n_nets && i < NETS; ++i) tab.net[i] = nets[i];
+    for (int i = n_nets; i < NETS; ++i) tab.net[i] = NetDev{};
+    switch (mem) {
+    case 0: eat_async_kernel<NETS, kArrShared><<<grid, block, smem, st>>>(tab, qa); break;
+    case 3: eat_async_kernel<NETS, kArrPerQuery><<<grid, block, smem, st>>>(tab, qa); break;
+    default: eat_async_kernel<NETS, kArrGlobal><<<grid, block, smem, st>>>(tab, qa); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_async(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
+                         int block, size_t smem, cudaStream_t st) {
+    if (n_nets == 1) return launch_async_t<1>(nets, n_nets, qa, mem, grid, block, smem, st);
+    return launch_async_t<EAT_MAX_NETS>(nets, n_nets, qa, mem, grid, block, smem, st);
 }
 
 template <int NETS>

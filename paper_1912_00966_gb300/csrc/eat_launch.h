@@ -38,6 +38,10 @@ struct QueryArgs {
 const void *cta_kernel(int nets, int mem);
 cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
                        int block, size_t smem, cudaStream_t st);
+// Asynchronous (round-free) kernel; mem 0, 1 or 3 as above (bitmap always shared).
+const void *async_kernel(int nets, int mem);
+cudaError_t launch_async(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
+                         int block, size_t smem, cudaStream_t st);
 cudaError_t launch_next_departure(const NetDev &N, const int32_t *types, const int32_t *times,
                                   int32_t n, int32_t *out, cudaStream_t st);
 

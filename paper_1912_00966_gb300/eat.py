@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libeat.so")
 EAT_INF = 2**31 - 1
 EAT_OK, EAT_ERR_INVALID, EAT_ERR_OOM, EAT_ERR_CUDA = 0, 1, 2, 3
 EAT_ERR_NO_CONVERGENCE, EAT_ERR_NO_DEVICE, EAT_ERR_WORKSPACE = 4, 5, 6
-EAT_MODE_AUTO, EAT_MODE_CTA, EAT_MODE_GRID = 0, 1, 2
+EAT_MODE_AUTO, EAT_MODE_CTA, EAT_MODE_GRID, EAT_MODE_ASYNC = 0, 1, 2, 3
 EAT_PLACE_AUTO, EAT_PLACE_SHARED, EAT_PLACE_GLOBAL_ARR, EAT_PLACE_GLOBAL = 0, 1, 2, 3
 EAT_SUBTRIPS_NONE, EAT_SUBTRIPS_SQRT_K, EAT_SUBTRIPS_SQRT_MEAN = 0, 1, 2
 EAT_MAX_NETS = 128
@@ -352,7 +352,7 @@ def eat_autotune(net: Net, sources, times, stream=None) -> dict:
     o = eat_query_opts()
     _check(_lib.eat_autotune(net.handle, _ptr(sources), _ptr(times), int(sources.shape[0]),
                              ctypes.byref(o), _stream_handle(stream)), "eat_autotune")
-    return {"block": o.block, "vwarp": o.vwarp}
+    return {"block": o.block, "vwarp": o.vwarp, "mode": o.mode}
 
 
 def eat_next_departure(net: Net, types, times, out, stream=None):

@@ -28,6 +28,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(eat):
     src, ts = _dev(q.source), _dev(q.t_s)
     shape = eat.eat_autotune(net, src, ts)
     assert shape["block"] in (256, 512, 1024) and shape["vwarp"] in (2, 4, 8, 16, 32)
+    assert shape["mode"] in (1, 3)
     out = torch.empty(128 * tt.n_stops, dtype=torch.int32, device="cuda")
     eat.eat_query_batch(net, src, ts, out)            # uses the tuned shape
     torch.cuda.synchronize()
