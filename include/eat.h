@@ -57,7 +57,7 @@ typedef struct eat_net eat_net;
 
 /* Input timetable: n_conn connections as four parallel int32 arrays in host
  * memory (Section II, Preliminaries).  Requirements, checked by eat_build:
- * 0 <= u, v < n_stops; dur >= 1; dep >= t0 (see eat_build_opts);
+ * 0 <= u, v < n_stops; 1 <= dur < 2^24; dep >= t0 (see eat_build_opts);
  * dep + dur < INT32_MAX.  Identical connections are merged.
  * `trip` (nullable) gives each connection's trip (vehicle run, Section III-G);
  * connections with a negative trip id belong to no trip.  The connections of a
@@ -128,13 +128,15 @@ typedef struct {
     const int32_t *cl;
     const uint32_t *ap;
     /* The device layout, derived from the arrays above (Section IV-A's CL stride y):
-     *   type_dev[4 * n_types]        {v, lambda, row_ptr[v], row_ptr[v+1]}
-     *   cluster_entries[8 * n_types * y]  entry (t, k) for cluster k_min + k:
-     *       {start0, sc0, start1, sc1, next, x, n, 0}: the cluster's n APs, the first
-     *       two inline (sc = difference << 16 | terms), the others at ap_extra[x ..];
-     *       next = first departure of the next non-empty cluster, EAT_INF if none
+     *   cluster_entries[8 * n_types * y]  entry (t, k) for cluster k_min + k, one
+     *       32-byte record: {rel0 | rel1 << 16, sc0, sc1, next, x/2 | n << 24, v,
+     *       lambda | d << 24, row_ptr[v]}: the cluster's n APs, the first two inline
+     *       with first terms base + rel, base = t0 + (k_min + k) * cluster_width, and
+     *       sc = difference << 16 | terms, the others at ap_extra[x ..] (n = 255: the
+     *       count is the first of two header slots there); next = first departure of
+     *       the next non-empty cluster, EAT_INF if none; v, lambda: head stop and
+     *       duration of type t; d: types leaving v (255: see row_ptr)
      *   ap_extra[2 * n_ap_extra] */
-    const int32_t *type_dev;
     const int32_t *cluster_entries;
     const uint32_t *ap_extra;
 } eat_net_view;
@@ -215,7 +217,7 @@ int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net *
  * IV-A) for callers that encode their own timetable.  All arrays are host memory.
  *   row_ptr[n_stops + 1]   types leaving stop u are row_ptr[u] .. row_ptr[u+1]-1
  *                          (row_ptr[0] = 0, row_ptr[n_stops] = n_types)
- *   type_v[n_types], type_dur[n_types]   head stop and duration (>= 1) of each
+ *   type_v[n_types], type_dur[n_types]   head stop and duration (1 .. 2^24-1) of each
  *                          connection type (Section III-B)
  *   type_cl_ptr[n_types + 1]   clusters of type t are type_cl_ptr[t] ..
  *                          type_cl_ptr[t+1]-1; every type has at least one

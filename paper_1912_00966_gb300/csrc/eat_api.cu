@@ -373,8 +373,7 @@ static int upload(eat_net *net) {
     }
     const HostNet &h = net->host;
     size_t off_row = 0;
-    size_t off_ty = align_up(off_row + ((size_t)h.n_stops + 1) * 4, 256);
-    size_t off_ce = align_up(off_ty + h.ty_dev.size() * 4, 256);
+    size_t off_ce = align_up(off_row + ((size_t)h.n_stops + 1) * 4, 256);
     size_t off_apx = align_up(off_ce + h.ce.size() * 4, 256);
     size_t total = align_up(off_apx + h.apx.size() * 4 + 16, 256);
     DeviceGuard guard(net->device);
@@ -389,7 +388,6 @@ static int upload(eat_net *net) {
     char *b = (char *)net->blob;
     struct Piece { size_t off; const void *src; size_t bytes; } pieces[] = {
         {off_row, h.row_ptr.data(), h.row_ptr.size() * 4},
-        {off_ty, h.ty_dev.data(), h.ty_dev.size() * 4},
         {off_ce, h.ce.data(), h.ce.size() * 4},
         {off_apx, h.apx.data(), h.apx.size() * 4},
     };
@@ -400,7 +398,6 @@ static int upload(eat_net *net) {
     }
     NetDev &d = net->dev;
     d.row_ptr = (const int32_t *)(b + off_row);
-    d.ty = (const int4 *)(b + off_ty);
     d.ce = (const int4 *)(b + off_ce);
     d.apx = (const uint2 *)(b + off_apx);
     d.n_stops = h.n_stops;
@@ -521,7 +518,6 @@ int eat_net_host_view(const eat_net *net, eat_net_view *out) {
     out->type_cl = net->host.type_cl.data();
     out->cl = net->host.cl.data();
     out->ap = net->host.ap.data();
-    out->type_dev = net->host.ty_dev.data();
     out->cluster_entries = net->host.ce.data();
     out->ap_extra = net->host.apx.data();
     return EAT_OK;

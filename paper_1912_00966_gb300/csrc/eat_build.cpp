@@ -177,6 +177,8 @@ int build_host(const eat_connections *c, int32_t width, int32_t t0, HostNet &h) 
             return fail(EAT_ERR_INVALID, "connection " + std::to_string(i) + ": departure too far after t0");
         if ((int64_t)dep + dur >= (int64_t)INT32_MAX)
             return fail(EAT_ERR_INVALID, "connection " + std::to_string(i) + ": arrival overflows int32");
+        if (dur >= kMaxDuration)
+            return fail(EAT_ERR_INVALID, "connection " + std::to_string(i) + ": duration must be < 2^24 s");
     }
 
     // Counting sort of the connections by tail stop.
@@ -323,6 +325,7 @@ int build_host_csr(const eat_csr_input *in, int32_t width, int32_t t0, HostNet &
         const int32_t v = in->type_v[t], lam = in->type_dur[t];
         if (v < 0 || v >= V) return bad("type head stop out of range", t);
         if (lam < 1) return bad("type duration must be >= 1", t);
+        if (lam >= kMaxDuration) return bad("type duration must be < 2^24 s", t);
         const int64_t c0 = in->type_cl_ptr[t], c1 = in->type_cl_ptr[t + 1];
         if (c1 <= c0) return bad("type without clusters", t);
         int32_t first = EAT_INF, last = INT32_MIN;
@@ -466,10 +469,13 @@ int add_subtrips(const eat_connections *c, int32_t scheme, std::vector<int32_t> 
 }
 
 // Device layout (see NetDev in eat_internal.h): one 32-byte entry per (type,
-// cluster) for every cluster of the network, with the cluster's first two APs
-// inline, the index of its further APs, and the first departure of the next
-// non-empty cluster, so one load of the entry answers getConnection for most
-// clusters (Algorithm 6 inside the hourly cluster of Section III-D).
+// cluster) for every cluster of the network, self-contained for a relaxation:
+// the cluster's first two APs (first terms relative to the cluster start), the
+// index and count of its further APs, the first departure of the next non-empty
+// cluster, and the type's head stop, duration and head row.  One load of the
+// entry answers getConnection for most clusters (Algorithm 6 inside the hourly
+// cluster of Section III-D) and gives everything Relax (Algorithm 3) and the
+// frontier push need.
 int build_fused(HostNet &h) {
     const int32_t T = h.n_types, W = h.width, t0 = h.t0;
     int32_t kmin = INT32_MAX, kmax = INT32_MIN;
@@ -491,14 +497,15 @@ int build_fused(HostNet &h) {
         const int32_t b = h.type_cl[t];
         int64_t extra = 0;   // each cluster's list padded to an even length (16-byte aligned)
         for (int32_t k = kf; k <= kl; ++k) {
-            const int32_t m = std::max(0, h.cl[b + k + 1] - h.cl[b + k] - 2);
+            const int32_t n = h.cl[b + k + 1] - h.cl[b + k];
+            const int32_t m = std::max(0, n - 2) + (n >= kCountOverflow ? 2 : 0);   // + count header
             extra += m + (m & 1);
         }
         xoff[t + 1] = xoff[t] + extra;
     }
-    if (xoff[T] >= INT32_MAX) return fail(EAT_ERR_INVALID, "too many APs for 32-bit indices");
+    if (xoff[T] / 2 >= (int64_t)1 << 24)
+        return fail(EAT_ERR_INVALID, "more than 2^25 APs beyond the two inline per cluster");
     try {
-        h.ty_dev.resize((size_t)T * 4);
         h.ce.assign((size_t)T * (size_t)Y * 8, 0);
         h.apx.resize((size_t)xoff[T] * 2);
     } catch (const std::bad_alloc &) {
@@ -507,11 +514,7 @@ int build_fused(HostNet &h) {
     auto fill = [&](int32_t t_begin, int32_t t_end) {
         for (int32_t t = t_begin; t < t_end; ++t) {
             const int32_t v = h.type_rec[4 * (size_t)t], lam = h.type_rec[4 * (size_t)t + 1];
-            int32_t *ty = &h.ty_dev[4 * (size_t)t];
-            ty[0] = v;
-            ty[1] = lam;
-            ty[2] = h.row_ptr[v];
-            ty[3] = h.row_ptr[v + 1];
+            const int32_t vb = h.row_ptr[v], dv = h.row_ptr[v + 1] - vb;
             const int32_t kf = (h.type_rec[4 * (size_t)t + 2] - t0) / W;
             const int32_t kl = (h.type_rec[4 * (size_t)t + 3] - t0) / W;
             const int32_t b = h.type_cl[t];
@@ -520,22 +523,35 @@ int build_fused(HostNet &h) {
             for (int32_t kr = 0; kr < Y; ++kr) {
                 int32_t *e = row + (size_t)kr * 8;
                 const int32_t k = kmin + kr;
+                const int64_t cbase = (int64_t)t0 + (int64_t)k * W;
                 int32_t lo = 0, n = 0;
                 if (k >= kf && k <= kl) {
                     lo = h.cl[b + k];
                     n = h.cl[b + k + 1] - lo;
                 }
-                e[0] = n >= 1 ? (int32_t)h.ap[2 * (size_t)lo] : EAT_INF;
+                const uint32_t rel0 = n >= 1 ? (uint32_t)((int64_t)h.ap[2 * (size_t)lo] - cbase) : 0u;
+                const uint32_t rel1 = n >= 2 ? (uint32_t)((int64_t)h.ap[2 * (size_t)(lo + 1)] - cbase) : 0u;
+                e[0] = (int32_t)(rel0 | (rel1 << 16));
                 e[1] = n >= 1 ? (int32_t)h.ap[2 * (size_t)lo + 1] : 0;
-                e[2] = n >= 2 ? (int32_t)h.ap[2 * (size_t)(lo + 1)] : EAT_INF;
-                e[3] = n >= 2 ? (int32_t)h.ap[2 * (size_t)(lo + 1) + 1] : 0;
-                e[5] = (int32_t)x;
-                e[6] = n;
-                for (int32_t j = 2; j < n; ++j, ++x) {
+                e[2] = n >= 2 ? (int32_t)h.ap[2 * (size_t)(lo + 1) + 1] : 0;
+                e[4] = (int32_t)(((uint32_t)(x / 2)) | ((uint32_t)std::min(n, kCountOverflow) << 24));
+                e[5] = v;
+                e[6] = (int32_t)((uint32_t)lam | ((uint32_t)std::min(dv, kCountOverflow) << 24));
+                e[7] = vb;
+                int64_t m = 0;
+                if (n >= kCountOverflow) {     // count header: two slots, count in the first
+                    h.apx[2 * (size_t)x] = (uint32_t)n;
+                    h.apx[2 * (size_t)x + 1] = 0u;
+                    h.apx[2 * (size_t)(x + 1)] = 0u;
+                    h.apx[2 * (size_t)(x + 1) + 1] = 0u;
+                    x += 2;
+                    m += 2;
+                }
+                for (int32_t j = 2; j < n; ++j, ++x, ++m) {
                     h.apx[2 * (size_t)x] = h.ap[2 * (size_t)(lo + j)];
                     h.apx[2 * (size_t)x + 1] = h.ap[2 * (size_t)(lo + j) + 1];
                 }
-                if (n > 2 && ((n - 2) & 1)) {     // padding entry, never examined
+                if (m & 1) {                   // padding entry, never examined
                     h.apx[2 * (size_t)x] = (uint32_t)EAT_INF;
                     h.apx[2 * (size_t)x + 1] = 0u;
                     ++x;
@@ -544,8 +560,9 @@ int build_fused(HostNet &h) {
             int32_t next = EAT_INF;
             for (int32_t kr = (int32_t)Y - 1; kr >= 0; --kr) {
                 int32_t *e = row + (size_t)kr * 8;
-                e[4] = next;
-                if (e[6] > 0) next = e[0];
+                e[3] = next;
+                if (((uint32_t)e[4] >> 24) > 0)
+                    next = (int32_t)(t0 + (int64_t)(kmin + kr) * W + (e[0] & 0xffff));
             }
         }
     };

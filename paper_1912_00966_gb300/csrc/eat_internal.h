@@ -17,20 +17,24 @@ namespace eat {
 // Device-side descriptor of one resident network (plain pointers into one blob).
 //
 // Device layout (derived from the logical arrays of HostNet by build_fused):
-//   ty[t]              int4 {v, lambda, row_ptr[v], row_ptr[v+1]} -- the head stop's
-//                      row range travels with the type, so a stop pushed onto the
-//                      frontier needs no further lookup to be expanded
-//   ce[t*y + k]        32-byte cluster entry of type t for cluster k_min + k, for every
-//                      cluster of the network (the paper's dense CL stride y):
-//                        int4 {start0, sc0, start1, sc1}   first two APs inline
-//                        int4 {next, x, n, 0}              next = first departure of the
-//                                                          next non-empty cluster (INF if
-//                                                          none), APs 3..n at apx[x ..]
-//                      sc = (difference << 16) | number of terms
-//   apx[]              uint2 {first term, sc} of the third and later APs of a cluster
+//   ce[t*y + k]   32-byte entry of type t for cluster k_min + k, for every cluster
+//                 of the network (the paper's dense CL stride y), read in one load:
+//                   int4 {rel0 | rel1 << 16, sc0, sc1, next}
+//                   int4 {x/2 | n << 24, v, lambda | d << 24, row_ptr[v]}
+//                 the cluster's n APs: the first two inline with first terms
+//                 base + rel (base = t0 + (k_min + k) * width) and
+//                 sc = (difference << 16) | terms, the others at apx[x ..] (x even);
+//                 n = 255 means more: the true count heads the list in two slots;
+//                 next = first departure of the next non-empty cluster (INF if none);
+//                 v, lambda: the type's head stop and duration; d: types leaving v
+//                 (255 = read row_ptr)
+//   apx[]         uint2 {first term, sc} of the third and later APs of a cluster
+//   row_ptr[V+1]  types leaving stop u are row_ptr[u] .. row_ptr[u+1]-1
+constexpr int32_t kCountOverflow = 255;
+constexpr int32_t kMaxDuration = 1 << 24;
+
 struct NetDev {
     const int32_t *row_ptr;   // [V + 1] types by tail stop
-    const int4 *ty;           // [T]
     const int4 *ce;           // [2 * T * y]
     const uint2 *apx;         // [n_apx]
     int32_t n_stops;
@@ -61,7 +65,6 @@ struct HostNet {
     std::vector<uint32_t> ap;        // 2 n_ap
     // Device layout (see NetDev).
     int32_t k_min = 0, y = 1;
-    std::vector<int32_t> ty_dev;     // 4 T
     std::vector<int32_t> ce;         // 8 T y
     std::vector<uint32_t> apx;       // 2 n_apx
 };

@@ -66,21 +66,23 @@ __device__ __forceinline__ int32_t ap_candidate(int32_t start, uint32_t sc, int3
 // getConnectionFromAPs (Algorithm 6) over the APs of one cluster entry, with the
 // Cluster-AP fallback of Section III-D: if the cluster has no departure >= e, the
 // answer is the first departure of the next non-empty cluster (`next`).
-// c0 = {start0, sc0, start1, sc1}, c1 = {next, x, n, 0}.
-__device__ __forceinline__ int32_t cluster_lookup(const int4 c0, const int4 c1, int32_t e,
-                                                  const uint2 *__restrict__ apx, int32_t &aps) {
-    const int32_t n = c1.z;
+// a = {rel0 | rel1 << 16, sc0, sc1, next}; n APs, the third and later at apx[x..];
+// base is the cluster's start time.
+__device__ __forceinline__ int32_t cluster_lookup(const int4 a, int32_t n, int32_t x, int32_t base,
+                                                  int32_t e, const uint2 *__restrict__ apx,
+                                                  int32_t &aps) {
     int32_t tc = kInf;
     if (n > 0) {
         ++aps;
-        tc = ap_candidate(c0.x, (uint32_t)c0.y, e);
-        if (n > 1 && c0.z < tc) {             // APs are ordered by first term
+        tc = ap_candidate(base + (a.x & 0xffff), (uint32_t)a.y, e);
+        const int32_t start1 = base + (int32_t)((uint32_t)a.x >> 16);
+        if (n > 1 && start1 < tc) {           // APs are ordered by first term
             ++aps;
-            tc = min(tc, ap_candidate(c0.z, (uint32_t)c0.w, e));
+            tc = min(tc, ap_candidate(start1, (uint32_t)a.z, e));
             // Further APs: batches of 8 loaded together (the list is 16-byte aligned
             // and padded to an even length), so one L2 round trip covers a batch.
             const int32_t m = n - 2;
-            const uint4 *p = reinterpret_cast<const uint4 *>(apx + c1.y);
+            const uint4 *p = reinterpret_cast<const uint4 *>(apx + x);
             for (int32_t j = 0; j < m; j += 8) {
                 uint4 r[4];
 #pragma unroll
@@ -96,7 +98,19 @@ __device__ __forceinline__ int32_t cluster_lookup(const int4 c0, const int4 c1, 
             }
         }
     }
-    return tc == kInf ? c1.x : tc;
+    return tc == kInf ? a.w : tc;
+}
+
+// Count and index of a cluster entry's APs (b = {x/2 | n << 24, ...}); a count of
+// 255 is read from the two-slot header that then starts the list.
+__device__ __forceinline__ void entry_aps(const int4 b, const uint2 *__restrict__ apx, int32_t &n,
+                                          int32_t &x) {
+    n = (int32_t)((uint32_t)b.x >> 24);
+    x = (b.x & 0xffffff) * 2;
+    if (n == kCountOverflow) {
+        n = (int32_t)__ldg(apx + x).x;
+        x += 2;
+    }
 }
 
 // Cluster slot of time e relative to the first stored cluster; e before the first
@@ -119,6 +133,11 @@ __device__ __forceinline__ int32_t cluster_slot(const NetDev &N, int32_t e) {
     return k < 0 ? 0 : k;
 }
 
+// Start time of stored cluster slot k.
+__device__ __forceinline__ int32_t cluster_base(const NetDev &N, int32_t k) {
+    return N.t0 + (N.k_min + k) * N.width;
+}
+
 // One 32-byte cluster entry in a single 256-bit load (sm_100 and later), read
 // through the non-coherent path: the entries never change during a query.
 __device__ __forceinline__ void load_entry(const int4 *c, int4 &a, int4 &b) {
@@ -135,7 +154,9 @@ __device__ __forceinline__ int32_t next_departure(const NetDev &N, int32_t t, in
     const int4 *c = N.ce + 2 * ((int64_t)t * N.y + k);
     int4 a, b;
     load_entry(c, a, b);
-    return cluster_lookup(a, b, e, N.apx, aps);
+    int32_t n, x;
+    entry_aps(b, N.apx, n, x);
+    return cluster_lookup(a, n, x, cluster_base(N, k), e, N.apx, aps);
 }
 
 enum { kArrGlobal = 0, kArrShared = 1, kArrPerQuery = 2 };
@@ -240,20 +261,23 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             auto relax = [&](int32_t e_u, int32_t k, int32_t t) {
                 ++c_types;
                 ++c_lookups;
-                const int4 ty = __ldg(N.ty + t);            // {v, lambda, row of v}
                 const int4 *c = N.ce + 2 * ((int64_t)t * N.y + k);
-                int4 ca, cb;
+                int4 ca, cb;                                // cb = {x|n, v, lambda|d, row of v}
                 load_entry(c, ca, cb);
-                const int32_t tc = cluster_lookup(ca, cb, e_u, N.apx, c_aps);
+                int32_t n, x;
+                entry_aps(cb, N.apx, n, x);
+                const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, k), e_u, N.apx, c_aps);
                 if (tc == kInf) return;                     // no departure left (Section IV-D)
                 ++c_evals;
-                const int32_t v = ty.x;
-                const int32_t cand = tc + ty.y;
+                const int32_t v = cb.y;
+                const int32_t cand = tc + (cb.z & 0xffffff);
                 if (cand >= load_arr(arr, v, arr_shared)) return;
                 const int32_t old = atomicMin(arr + v, cand);
                 if (cand >= old) return;
                 ++c_relax;
-                const int32_t d = ty.w - ty.z;              // types leaving v
+                int32_t d = (int32_t)((uint32_t)cb.z >> 24);  // types leaving v
+                if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - cb.w;
+                const int4 ty = make_int4(v, 0, cb.w, cb.w + d);
                 if (d <= 0) return;
                 const uint32_t bit = 1u << (v & 31);
                 if (atomicOr(pmask + (v >> 5), bit) & bit) return;   // already queued
@@ -489,20 +513,21 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
                 const int32_t eu = st_e[lo], kk = st_k[lo];
                 ++c_types;
                 ++c_lookups;
-                const int4 ty = __ldg(N.ty + t);             // {v, lambda, row of v}
                 const int4 *c = N.ce + 2 * ((int64_t)t * N.y + kk);
-                int4 ca, cb;
+                int4 ca, cb;                                 // cb = {x|n, v, lambda|d, row of v}
                 load_entry(c, ca, cb);
-                const int32_t tc = cluster_lookup(ca, cb, eu, N.apx, c_aps);
+                int32_t n, x;
+                entry_aps(cb, N.apx, n, x);
+                const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, kk), eu, N.apx, c_aps);
                 if (tc == kInf) continue;
                 ++c_evals;
-                const int32_t v = ty.x;
-                const int32_t cand = tc + ty.y;
+                const int32_t v = cb.y;
+                const int32_t cand = tc + (cb.z & 0xffffff);
                 if (cand >= load_arr(arr, v, arr_shared)) continue;
                 const int32_t old = atomicMin(arr + v, cand);
                 if (cand >= old) continue;
                 ++c_relax;
-                if (ty.w - ty.z <= 0) continue;            // v has no outgoing types
+                if (((uint32_t)cb.z >> 24) == 0) continue;  // v has no outgoing types
                 const uint32_t bit = 1u << (v & 31);
                 atomicAdd(&s_work, 1);                      // count before publishing
                 __threadfence_block();

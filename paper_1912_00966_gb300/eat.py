@@ -63,7 +63,7 @@ class eat_stats(ctypes.Structure):
 
 class eat_net_view(ctypes.Structure):
     _fields_ = [("row_ptr", _vp), ("type_rec", _vp), ("type_cl", _vp), ("cl", _vp),
-                ("ap", _vp), ("type_dev", _vp), ("cluster_entries", _vp), ("ap_extra", _vp)]
+                ("ap", _vp), ("cluster_entries", _vp), ("ap_extra", _vp)]
 
 
 class eat_counters(ctypes.Structure):
@@ -275,7 +275,6 @@ def eat_net_host_view(net: Net) -> dict:
         "type_cl": arr(view.type_cl, T, np.int32),
         "cl": arr(view.cl, st["n_cl"], np.int32),
         "ap": arr(view.ap, 2 * st["n_ap"], np.uint32).reshape(-1, 2),
-        "type_dev": arr(view.type_dev, 4 * T, np.int32).reshape(T, 4),
         "cluster_entries": arr(view.cluster_entries, 8 * T * st["y"], np.int32).reshape(T, st["y"], 8),
         "ap_extra": arr(view.ap_extra, 2 * st["n_ap_extra"], np.uint32).reshape(-1, 2),
     }

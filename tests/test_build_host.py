@@ -159,8 +159,7 @@ def test_device_cluster_entries_match_oracle(make, width, t0):
     hv, st = eat.eat_net_host_view(net), eat.eat_get_stats(net)
     W = width or 3600
     types = oracle.connection_types(tt)
-    rp, rec, tyd, ce, apx = (hv[k] for k in ("row_ptr", "type_rec", "type_dev",
-                                             "cluster_entries", "ap_extra"))
+    rp, rec, ce, apx = (hv[k] for k in ("row_ptr", "type_rec", "cluster_entries", "ap_extra"))
     y, kmin = st["y"], st["k_min"]
     all_k = [(d - t0) // W for ds in types.values() for d in ds]
     assert kmin == min(all_k) and y == max(all_k) - kmin + 1
@@ -172,23 +171,53 @@ def test_device_cluster_entries_match_oracle(make, width, t0):
     for u in range(st["n_stops"]):
         for t in range(rp[u], rp[u + 1]):
             v, lam = int(rec[t][0]), int(rec[t][1])
-            assert tyd[t].tolist() == [v, lam, rp[v], rp[v + 1]]
             deps = types[(u, v, lam)]
             clusters = oracle.cluster_sets(deps, width=W, t0=t0)
             for kr in range(y):
                 k = kmin + kr
-                e = ce[t, kr]
-                n = int(e[6])
+                base = t0 + k * W
+                e = [int(x_) & 0xFFFFFFFF for x_ in ce[t, kr]]
+                n, x = e[4] >> 24, (e[4] & 0xFFFFFF) * 2
+                if n == 255:
+                    n, x = int(apx[x][0]), x + 2
+                d = e[6] >> 24
+                assert (e[5], e[6] & 0xFFFFFF, e[7]) == (v, lam, rp[v])
+                assert d == min(255, rp[v + 1] - rp[v])
                 got = []
                 if n >= 1:
-                    got.append(dec(e[0], int(e[1]) & 0xFFFFFFFF))
+                    got.append(dec(base + (e[0] & 0xFFFF), e[1]))
                 if n >= 2:
-                    got.append(dec(e[2], int(e[3]) & 0xFFFFFFFF))
+                    got.append(dec(base + (e[0] >> 16), e[2]))
                 for j in range(2, n):
-                    got.append(dec(apx[e[5] + j - 2][0], int(apx[e[5] + j - 2][1])))
+                    got.append(dec(apx[x + j - 2][0], int(apx[x + j - 2][1])))
                 assert got == ap_cover(clusters.get(k, []))
-                later = [d for d in deps if (d - t0) // W > k]
-                assert int(e[4]) == (min(later) if later else INF)
+                later = [dd for dd in deps if (dd - t0) // W > k]
+                assert e[3] == (min(later) if later else INF)
+
+
+def test_count_overflow_header():
+    """A cluster needing more than 254 APs keeps its count in the header of its AP list.
+    Integers whose base-3 digits are all 0 or 1 contain no three-term arithmetic
+    progression, so the greedy cover needs about one AP per two departures."""
+    vals = [sum(((i >> b) & 1) * 3 ** b for b in range(10)) for i in range(1024)]
+    deps = np.array(sorted(vals), dtype=np.int32)
+    n = deps.shape[0]
+    z = np.zeros(n, np.int32)
+    tt = synth.Timetable("dense", 2, z, z + 1, deps, z + 5, z, z)
+    net = _build(tt, cluster_width=65535)
+    ce = eat.eat_net_host_view(net)["cluster_entries"]
+    e4 = int(ce[0, 0, 4]) & 0xFFFFFFFF
+    n_ap = eat.eat_get_stats(net)["n_ap"]
+    assert n_ap >= 255 and e4 >> 24 == 255
+    apx = eat.eat_net_host_view(net)["ap_extra"]
+    assert int(apx[(e4 & 0xFFFFFF) * 2][0]) == n_ap
+
+
+def test_long_duration_rejected():
+    z = np.zeros(1, np.int32)
+    with pytest.raises(eat.EatError) as ei:
+        eat.eat_build(2, z, z + 1, z + 10, z + (1 << 24), device=-1)
+    assert "2^24" in str(ei.value)
 
 
 # ------------------------------------------------------------------ sub-trips (Section III-G)

@@ -349,3 +349,20 @@ def test_ragged_batch_with_per_query_placement(eat, small):
                               torch.as_tensor(offs).cuda())
     torch.cuda.synchronize()
     assert np.array_equal(dev.cpu().numpy(), out)
+
+
+def test_lookup_through_count_overflow_header(eat):
+    """A cluster of > 254 APs (its count in the AP-list header) still answers exactly."""
+    vals = [sum(((i >> b) & 1) * 3 ** b for b in range(10)) for i in range(1024)]
+    deps = np.array(sorted(vals), dtype=np.int32)
+    z = np.zeros(deps.shape[0], np.int32)
+    tt = synth.Timetable("dense", 2, z, z + 1, deps, z + 5, z, z)
+    net = eat.eat_build(2, tt.u, tt.v, tt.dep, tt.dur, cluster_width=65535, device=0)
+    times = np.concatenate([deps - 1, deps, deps + 1, [-3, 0, 70000]]).astype(np.int32)
+    out = torch.empty(times.shape[0], dtype=torch.int32, device="cuda")
+    eat.eat_next_departure(net, _dev(np.zeros_like(times)), _dev(times), out)
+    want = [oracle.next_departure(deps.tolist(), int(e)) for e in times]
+    assert out.cpu().numpy().tolist() == want
+    for t_s in (0, 5000, 59000):
+        got = eat.eat_query(net, 0, t_s)
+        assert np.array_equal(got, oracle.csa(oracle.SortedConnections(tt), 0, t_s))
