@@ -598,9 +598,12 @@ def run_ours(args):
 
     peak, peak_kind = measured_peak()
     achieved = per_launch / (mean_ms / 1e3) / 1e9
+    mode_used = (tuned or {}).get("mode", args.mode)
+    kernel_name = "eat_async_kernel" if mode_used == eat.EAT_MODE_ASYNC else "eat_cta_kernel"
     h = kernel_hash()
     traffic = None
-    if args.workload in NCU_TRAFFIC_PER_QUERY and NCU_TRAFFIC_PER_QUERY[args.workload][0] == h:
+    if (kernel_name == "eat_cta_kernel" and args.workload in NCU_TRAFFIC_PER_QUERY
+            and NCU_TRAFFIC_PER_QUERY[args.workload][0] == h):
         traffic = NCU_TRAFFIC_PER_QUERY[args.workload][1] * batch
 
     cpu = None
@@ -624,12 +627,16 @@ def run_ours(args):
         "dtype": "int32", "data": "synthetic",
         "config": describe(args.workload, tt, batch),
         "e2e": {"value": n_q / e2e_s, "unit": "queries/s",
-                "h2d_bytes_per_step": 2 * 4 * batch, "d2h_bytes_per_step": 4 * V * batch},
+                "h2d_bytes_per_step": 2 * 4 * batch, "d2h_bytes_per_step": 4 * V * batch,
+                "path": "blocking eat_query_batch on page-locked host buffers: when the "
+                        "arrivals fit in shared memory the kernel reads the queries and "
+                        "writes each finished row into host memory in place (NVLink-C2C), "
+                        "else the library stages rows with copies after the launch"},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} (burst copy)",
-                     "kernel": "eat_cta_kernel", "alg_bytes_per_launch": per_launch},
+                     "kernel": kernel_name, "alg_bytes_per_launch": per_launch},
         "cpu_baseline": cpu,
         "connections_relaxed_per_s": tot["types"] / (gpu_s / world),
         "subtrips": {0: "none", 1: "sqrt(k) per trip", 2: "sqrt(mean trip length)"}[args.subtrips],

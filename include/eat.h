@@ -272,7 +272,8 @@ int eat_net_host_view(const eat_net *net, eat_net_view *out);
 /*
  * eat_query -- one query (s, t_s), blocking (Algorithms 2-5, Section III-D).
  *   arr_out  [n_stops] int32, host or device memory: arr_out[v] = e[v],
- *            EAT_INF if v is unreachable; arr_out[s] = t_s.
+ *            EAT_INF if v is unreachable; arr_out[s] = t_s.  Page-locked host
+ *            memory is written in place when the arrivals fit in shared memory.
  *   counters optional (NULL), host memory.
  * Runs on the legacy default stream with the network's own workspace, so
  * concurrent eat_query calls on one network are serialised internally.
@@ -304,8 +305,13 @@ size_t eat_workspace_bytes(const eat_net *const *nets, int32_t n_nets, int32_t n
  *   opts            may be NULL.
  *   stream          cudaStream_t to run on.
  * If every buffer is device memory the call is asynchronous on `stream`.  If
- * any is host memory the call stages through device memory and returns after
- * the results are in arr_out.  Per-query round-cap failures are reported
+ * any is host memory the call returns after the results are in arr_out: when
+ * arr_out is page-locked host memory mapped for the device (cudaHostAlloc,
+ * cudaHostRegister) and the arrivals fit in shared memory, the kernel writes
+ * each query's row straight into arr_out as the query finishes (and reads
+ * page-locked sources/times in place), so the transfer overlaps the other
+ * queries; otherwise host buffers are staged through device memory with
+ * copies before and after the launch.  Per-query round-cap failures are reported
  * only through opts->status (the return value covers launch errors).
  * Errors: EAT_ERR_INVALID, EAT_ERR_WORKSPACE, EAT_ERR_NO_DEVICE, EAT_ERR_CUDA,
  * EAT_ERR_OOM.

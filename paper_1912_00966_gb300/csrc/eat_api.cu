@@ -49,6 +49,18 @@ static bool is_device_ptr(const void *p) {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Device address of page-locked host memory that the GPU may read and write in place
+// (mapped pinned memory, reached over NVLink-C2C on Grace systems), else nullptr.
+static void *mapped_host_ptr(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // ------------------------------------------------------------------ launch planning
 
 struct DeviceInfo {
@@ -550,7 +562,9 @@ int eat_query(const eat_net *net, int32_t s, int32_t t_s, int32_t *arr_out,
     int rc = make_plan(net->device, net->host.n_stops, 1, 1, nullptr, p, -1, net);
     if (rc) return rc;
     DeviceGuard guard(net->device);
-    const bool dev_out = is_device_ptr(arr_out);
+    // A page-locked host row is written in place when the arrivals live in shared memory.
+    int32_t *const out_map = p.mem == 0 ? (int32_t *)mapped_host_ptr(arr_out) : nullptr;
+    const bool dev_out = is_device_ptr(arr_out) || out_map;
     const size_t rows = dev_out ? 0 : align_up((size_t)net->host.n_stops * 4, 256);
     rc = ensure_buffer(net->ws, net->ws_bytes, p.ws_bytes + rows + 256);
     if (rc) return rc;
@@ -558,7 +572,7 @@ int eat_query(const eat_net *net, int32_t s, int32_t t_s, int32_t *arr_out,
     // Internal scratch after the plan's workspace: [src, t_s, status, pad][counters][row].
     int32_t *io = (int32_t *)(w + p.ws_bytes);
     eat_counters *cnt = (eat_counters *)(w + p.ws_bytes + 64);
-    int32_t *row = dev_out ? arr_out : (int32_t *)(w + p.ws_bytes + 256);
+    int32_t *row = out_map ? out_map : dev_out ? arr_out : (int32_t *)(w + p.ws_bytes + 256);
     int32_t h_io[2] = {s, t_s};
     cudaError_t e = cudaMemcpyAsync(io, h_io, sizeof(h_io), cudaMemcpyHostToDevice, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
@@ -686,23 +700,39 @@ int eat_query_batch(const eat_net *net, const int32_t *sources, const int32_t *t
         return run_batch(nets, 1, nullptr, sources, times, n, arr_out, nullptr, workspace,
                          workspace_bytes, opts, st, nullptr, nullptr);
     }
-    // At least one host buffer: stage through device memory, then synchronise.
+    // At least one host buffer.  Page-locked (mapped) host buffers are used in place
+    // when the query's arrivals live in shared memory: the kernel reads the queries
+    // and writes each finished row straight to host memory, so the rows travel while
+    // other queries still run.  Otherwise host buffers are staged through device
+    // memory.  Either way the call returns after the rows are in arr_out.
     if (!d_src)
         for (int32_t i = 0; i < n; ++i)
             if (sources[i] < 0 || sources[i] >= net->host.n_stops)
                 return fail(EAT_ERR_INVALID, "source out of range");
     std::lock_guard<std::mutex> g(net->ws_lock);
+    int32_t *out_map = d_out ? nullptr : (int32_t *)mapped_host_ptr(arr_out);
+    if (out_map) {
+        Plan p;
+        if (make_plan(net->device, net->host.n_stops, n, 1, opts, p, -1, net) != EAT_OK || p.mem != 0) {
+            clear_error();
+            out_map = nullptr;                         // arrivals would live in the row
+        }
+    }
+    const int32_t *src_map = (out_map && !d_src) ? (const int32_t *)mapped_host_ptr(sources) : nullptr;
+    const int32_t *ts_map = (out_map && !d_ts) ? (const int32_t *)mapped_host_ptr(times) : nullptr;
+    const bool direct_out = d_out || out_map;
     const size_t in_bytes = align_up((size_t)n * 4, 256);
     const size_t out_bytes = (size_t)n * (size_t)net->host.n_stops * 4;
-    int rc = ensure_buffer(net->stage, net->stage_bytes, 2 * in_bytes + (d_out ? 0 : out_bytes));
+    int rc = ensure_buffer(net->stage, net->stage_bytes, 2 * in_bytes + (direct_out ? 0 : out_bytes));
     if (rc) return rc;
     char *sb = (char *)net->stage;
-    const int32_t *src_d = d_src ? sources : (const int32_t *)sb;
-    const int32_t *ts_d = d_ts ? times : (const int32_t *)(sb + in_bytes);
-    int32_t *out_d = d_out ? arr_out : (int32_t *)(sb + 2 * in_bytes);
+    const int32_t *src_d = d_src ? sources : src_map ? src_map : (const int32_t *)sb;
+    const int32_t *ts_d = d_ts ? times : ts_map ? ts_map : (const int32_t *)(sb + in_bytes);
+    int32_t *out_d = d_out ? arr_out : out_map ? out_map : (int32_t *)(sb + 2 * in_bytes);
     cudaError_t e = cudaSuccess;
-    if (!d_src) e = cudaMemcpyAsync((void *)src_d, sources, (size_t)n * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !d_ts)
+    if (!d_src && !src_map)
+        e = cudaMemcpyAsync((void *)src_d, sources, (size_t)n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !d_ts && !ts_map)
         e = cudaMemcpyAsync((void *)ts_d, times, (size_t)n * 4, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     void *ws = workspace;
@@ -718,7 +748,7 @@ int eat_query_batch(const eat_net *net, const int32_t *sources, const int32_t *t
     rc = run_batch(nets, 1, nullptr, src_d, ts_d, n, out_d, nullptr, ws, wsb, opts, st, nullptr,
                    nullptr);
     if (rc) return rc;
-    if (!d_out) e = cudaMemcpyAsync(arr_out, out_d, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (!direct_out) e = cudaMemcpyAsync(arr_out, out_d, out_bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "eat_query_batch");
     return EAT_OK;

@@ -108,6 +108,27 @@ def test_host_buffers_match_device(eat, small):
     assert np.array_equal(pinned.numpy(), want)
 
 
+@pytest.mark.parametrize("mode", [1, 3])
+def test_pinned_host_rows_written_in_place(eat, city, mode):
+    """Page-locked host queries and rows (the kernel reads and writes them in place)
+    equal the oracle, also when the arrivals cannot stay in shared memory (then the
+    rows are staged) and for a single eat_query into a page-locked row."""
+    q = synth.random_queries(city.tt, 256, 0x9A + mode)
+    src = torch.as_tensor(q.source).pin_memory()
+    ts = torch.as_tensor(q.t_s).pin_memory()
+    want = city.oracle_rows(q.source, q.t_s)
+    rows = torch.full((256, city.V), -7, dtype=torch.int32).pin_memory()
+    eat.eat_query_batch(city.net, src, ts, rows, mode=mode)
+    assert np.array_equal(rows.numpy(), want)
+    rows.fill_(-7)
+    eat.eat_query_batch(city.net, src, ts, rows, placement=eat.EAT_PLACE_GLOBAL_ARR)
+    assert np.array_equal(rows.numpy(), want)
+    one = torch.full((city.V,), -7, dtype=torch.int32).pin_memory()
+    for i in (0, 77, 255):
+        eat.eat_query(city.net, int(q.source[i]), int(q.t_s[i]), one)
+        assert np.array_equal(one.numpy(), want[i])
+
+
 @pytest.mark.parametrize("seed", range(30))
 def test_tiny_random_nets_all_sources(eat, seed):
     tt = synth.tiny_random(2 + seed % 13, 1 + (seed * 37) % 300, 500 + seed, t_max=300 + 50 * seed,
