@@ -208,7 +208,10 @@ def run_ours_ragged(args):
                    "l2": "flushed before every step (256 MB write)", "parallelism": "replicas",
                    "method": "Cluster-AP fixpoint, one launch over all networks"},
         "e2e": {"value": n_q / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 20 * Q,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "path": "blocking eat_query_batch_multi: query arrays staged to the device, "
+                        "each converged row written by the kernel into the page-locked host "
+                        "output in place (NVLink-C2C)"},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
@@ -628,10 +631,10 @@ def run_ours(args):
         "config": describe(args.workload, tt, batch),
         "e2e": {"value": n_q / e2e_s, "unit": "queries/s",
                 "h2d_bytes_per_step": 2 * 4 * batch, "d2h_bytes_per_step": 4 * V * batch,
-                "path": "blocking eat_query_batch on page-locked host buffers: when the "
-                        "arrivals fit in shared memory the kernel reads the queries and "
-                        "writes each finished row into host memory in place (NVLink-C2C), "
-                        "else the library stages rows with copies after the launch"},
+                "path": "blocking eat_query_batch on page-locked host buffers: the kernel "
+                        "reads the queries and writes each converged row into host memory in "
+                        "place (NVLink-C2C); arrivals not in shared memory use a device row "
+                        "per persistent block meanwhile"},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

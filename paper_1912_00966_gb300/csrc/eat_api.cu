@@ -307,7 +307,15 @@ static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net
     qa.smem_mask_off = p.smem_mask_off;
     qa.smem_q_off = p.smem_q_off;
     qa.smem_arr_cap = p.smem_arr_cap;
+    qa.arr_rows = nullptr;
+    qa.arr_rows_stride = 0;
     return qa;
+}
+
+// Per-block arrival rows needed when a plan keeps some arrivals out of shared memory
+// and the output rows are host memory (0 when every query's arrivals are shared).
+static size_t arr_rows_bytes(const Plan &p) {
+    return p.mem == 0 ? 0 : (size_t)p.grid * align_up((size_t)p.vmax, 64) * 4;
 }
 
 static int ensure_buffer(void *&buf, size_t &cap, size_t need) {
@@ -329,7 +337,8 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
                      const int32_t *src, const int32_t *ts, int32_t n, int32_t *arr_out,
                      const int64_t *arr_off, void *ws, size_t ws_bytes,
                      const eat_query_opts *o, cudaStream_t st, int32_t *status_override,
-                     eat_counters *counters_override) {
+                     eat_counters *counters_override, int32_t *arr_rows = nullptr,
+                     size_t arr_rows_size = 0) {
     const int dev = nets[0]->device;
     int32_t vmax = 0, vmin = INT32_MAX;
     for (int i = 0; i < n_nets; ++i) {
@@ -347,6 +356,11 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
     QueryArgs qa = make_args(p, p.grid, (char *)ws, net_idx, src, ts, n, n_nets, arr_out, arr_off,
                              cap, status_override ? status_override : (o ? o->status : nullptr),
                              counters_override ? counters_override : (o ? o->counters : nullptr));
+    if (arr_rows && p.mem != 0) {
+        if (arr_rows_size < arr_rows_bytes(p)) return fail(EAT_ERR_INVALID, "arrival rows too small");
+        qa.arr_rows = arr_rows;
+        qa.arr_rows_stride = (int64_t)align_up((size_t)p.vmax, 64);
+    }
     DeviceGuard guard(dev);
     cudaError_t e = cudaMemsetAsync(qa.work, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -562,9 +576,10 @@ int eat_query(const eat_net *net, int32_t s, int32_t t_s, int32_t *arr_out,
     int rc = make_plan(net->device, net->host.n_stops, 1, 1, nullptr, p, -1, net);
     if (rc) return rc;
     DeviceGuard guard(net->device);
-    // A page-locked host row is written in place when the arrivals live in shared memory.
-    int32_t *const out_map = p.mem == 0 ? (int32_t *)mapped_host_ptr(arr_out) : nullptr;
-    const bool dev_out = is_device_ptr(arr_out) || out_map;
+    // A page-locked host row is written in place; arrivals that do not fit in shared
+    // memory then live in the device row below and are copied over at the end.
+    const bool dev_out = is_device_ptr(arr_out);
+    int32_t *const out_map = dev_out ? nullptr : (int32_t *)mapped_host_ptr(arr_out);
     const size_t rows = dev_out ? 0 : align_up((size_t)net->host.n_stops * 4, 256);
     rc = ensure_buffer(net->ws, net->ws_bytes, p.ws_bytes + rows + 256);
     if (rc) return rc;
@@ -572,19 +587,20 @@ int eat_query(const eat_net *net, int32_t s, int32_t t_s, int32_t *arr_out,
     // Internal scratch after the plan's workspace: [src, t_s, status, pad][counters][row].
     int32_t *io = (int32_t *)(w + p.ws_bytes);
     eat_counters *cnt = (eat_counters *)(w + p.ws_bytes + 64);
-    int32_t *row = out_map ? out_map : dev_out ? arr_out : (int32_t *)(w + p.ws_bytes + 256);
+    int32_t *const dev_row = (int32_t *)(w + p.ws_bytes + 256);
+    int32_t *row = dev_out ? arr_out : out_map ? out_map : dev_row;
     int32_t h_io[2] = {s, t_s};
     cudaError_t e = cudaMemcpyAsync(io, h_io, sizeof(h_io), cudaMemcpyHostToDevice, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     const eat_net *nets[1] = {net};
     rc = run_batch(nets, 1, nullptr, io, io + 1, 1, row, nullptr, w, p.ws_bytes, nullptr, 0,
-                   io + 2, cnt);
+                   io + 2, cnt, out_map ? dev_row : nullptr, rows);
     if (rc) return rc;
     int32_t st_h = 0;
     e = cudaMemcpyAsync(&st_h, io + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, 0);
     if (e == cudaSuccess && counters)
         e = cudaMemcpyAsync(counters, cnt, sizeof(eat_counters), cudaMemcpyDeviceToHost, 0);
-    if (e == cudaSuccess && !dev_out)
+    if (e == cudaSuccess && !dev_out && !out_map)
         e = cudaMemcpyAsync(arr_out, row, (size_t)net->host.n_stops * 4, cudaMemcpyDeviceToHost, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return cuda_fail(e, "eat_query");
@@ -640,8 +656,26 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
         out_elems = std::max(out_elems, arr_offsets[i] + nets[net_idx[i]]->host.n_stops);
     }
     std::lock_guard<std::mutex> g(nets[0]->ws_lock);
+    // A page-locked (mapped) arr_out is written in place by the kernel, with per-block
+    // device rows for arrivals that do not fit in shared memory; else rows are staged.
+    int32_t *out_map = dev_out ? nullptr : (int32_t *)mapped_host_ptr(arr_out);
+    size_t rows_bytes = 0;
+    if (out_map) {
+        int32_t vmax = 0, vmin = INT32_MAX;
+        for (int i = 0; i < n_nets; ++i) {
+            vmax = std::max(vmax, nets[i]->host.n_stops);
+            vmin = std::min(vmin, nets[i]->host.n_stops);
+        }
+        Plan p;
+        if (make_plan(nets[0]->device, vmax, n, n_nets, opts, p, vmin, n_nets == 1 ? nets[0] : nullptr)) {
+            clear_error();
+            out_map = nullptr;
+        } else {
+            rows_bytes = arr_rows_bytes(p);
+        }
+    }
     const size_t in_bytes = align_up((size_t)n * 4, 256) * 3 + align_up((size_t)n * 8, 256);
-    const size_t out_bytes = dev_out ? 0 : (size_t)out_elems * 4;
+    const size_t out_bytes = dev_out ? 0 : out_map ? rows_bytes : (size_t)out_elems * 4;
     int rc = ensure_buffer(nets[0]->stage, nets[0]->stage_bytes, in_bytes + out_bytes);
     if (rc) return rc;
     char *sb = (char *)nets[0]->stage;
@@ -664,11 +698,12 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
         ws = nets[0]->ws;
         wsb = nets[0]->ws_bytes;
     }
-    int32_t *out_d = dev_out ? arr_out : (int32_t *)(sb + in_bytes);
+    int32_t *out_d = dev_out ? arr_out : out_map ? out_map : (int32_t *)(sb + in_bytes);
     rc = run_batch(nets, n_nets, d_idx, d_src, d_ts, n, out_d, d_off, ws, wsb, opts, st,
-                   nullptr, nullptr);
+                   nullptr, nullptr, rows_bytes ? (int32_t *)(sb + in_bytes) : nullptr, rows_bytes);
     if (rc) return rc;
-    if (!dev_out) e = cudaMemcpyAsync(arr_out, out_d, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (!dev_out && !out_map)
+        e = cudaMemcpyAsync(arr_out, out_d, out_bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "eat_query_batch_multi");
     return EAT_OK;
@@ -700,22 +735,26 @@ int eat_query_batch(const eat_net *net, const int32_t *sources, const int32_t *t
         return run_batch(nets, 1, nullptr, sources, times, n, arr_out, nullptr, workspace,
                          workspace_bytes, opts, st, nullptr, nullptr);
     }
-    // At least one host buffer.  Page-locked (mapped) host buffers are used in place
-    // when the query's arrivals live in shared memory: the kernel reads the queries
-    // and writes each finished row straight to host memory, so the rows travel while
-    // other queries still run.  Otherwise host buffers are staged through device
-    // memory.  Either way the call returns after the rows are in arr_out.
+    // At least one host buffer.  Page-locked (mapped) host buffers are used in place:
+    // the kernel reads the queries and writes each converged row straight to host
+    // memory, so the rows travel while other queries still run (arrivals that do not
+    // fit in shared memory live in a per-block device row meanwhile).  Other host
+    // buffers are staged through device memory.  Either way the call returns after
+    // the rows are in arr_out.
     if (!d_src)
         for (int32_t i = 0; i < n; ++i)
             if (sources[i] < 0 || sources[i] >= net->host.n_stops)
                 return fail(EAT_ERR_INVALID, "source out of range");
     std::lock_guard<std::mutex> g(net->ws_lock);
     int32_t *out_map = d_out ? nullptr : (int32_t *)mapped_host_ptr(arr_out);
+    size_t rows_bytes = 0;                       // per-block arrival rows (host rows only)
     if (out_map) {
         Plan p;
-        if (make_plan(net->device, net->host.n_stops, n, 1, opts, p, -1, net) != EAT_OK || p.mem != 0) {
+        if (make_plan(net->device, net->host.n_stops, n, 1, opts, p, -1, net) != EAT_OK) {
             clear_error();
-            out_map = nullptr;                         // arrivals would live in the row
+            out_map = nullptr;
+        } else {
+            rows_bytes = arr_rows_bytes(p);
         }
     }
     const int32_t *src_map = (out_map && !d_src) ? (const int32_t *)mapped_host_ptr(sources) : nullptr;
@@ -723,7 +762,8 @@ int eat_query_batch(const eat_net *net, const int32_t *sources, const int32_t *t
     const bool direct_out = d_out || out_map;
     const size_t in_bytes = align_up((size_t)n * 4, 256);
     const size_t out_bytes = (size_t)n * (size_t)net->host.n_stops * 4;
-    int rc = ensure_buffer(net->stage, net->stage_bytes, 2 * in_bytes + (direct_out ? 0 : out_bytes));
+    int rc = ensure_buffer(net->stage, net->stage_bytes,
+                           2 * in_bytes + (direct_out ? rows_bytes : out_bytes));
     if (rc) return rc;
     char *sb = (char *)net->stage;
     const int32_t *src_d = d_src ? sources : src_map ? src_map : (const int32_t *)sb;
@@ -746,7 +786,7 @@ int eat_query_batch(const eat_net *net, const int32_t *sources, const int32_t *t
         wsb = net->ws_bytes;
     }
     rc = run_batch(nets, 1, nullptr, src_d, ts_d, n, out_d, nullptr, ws, wsb, opts, st, nullptr,
-                   nullptr);
+                   nullptr, rows_bytes ? (int32_t *)(sb + 2 * in_bytes) : nullptr, rows_bytes);
     if (rc) return rc;
     if (!direct_out) e = cudaMemcpyAsync(arr_out, out_d, out_bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -21,17 +21,19 @@
 // writes one (v, type) item per connection type leaving v into shared memory, so
 // the next round hands every thread one (stop, type) pair: the paper's one thread
 // per connection type (Algorithm 5), restricted to the active tails.  Per item the
-// dependent memory chain is one L2 round trip: the type record and its 32-byte
-// cluster entry are independent loads (the entry's address depends only on the
-// type and e[u]'s cluster); e[u], e[v] and the frontier live in shared memory.
+// dependent memory chain is one L2 round trip: its 32-byte cluster entry (whose
+// address depends only on the type and e[u]'s cluster) carries the head stop,
+// duration and head row as well; e[u], e[v] and the frontier live in shared memory.
 // Stops whose items do not fit spill to a global queue and are expanded by
 // `vwarp`-lane sub-warps (Section III-F's virtual warps).
 //
-// Buffers per query: arrivals in shared memory (ARR = kArrShared), in the
-// output row (kArrGlobal), or per query whichever the query's network allows
+// Buffers per query: arrivals in shared memory (ARR = kArrShared), in global
+// memory (kArrGlobal: the output row, or the block's scratch row when the output
+// is host memory), or per query whichever the query's network allows
 // (kArrPerQuery: shared when n_stops <= smem_arr_cap, for batches over networks
 // of uneven size); two frontier bitmaps (this round's pushes, last round's) in
-// shared memory when they fit (SMEM_MASK).
+// shared memory when they fit (SMEM_MASK).  Arrivals not kept in the output row
+// are copied there when the query converges.
 #include <cuda_runtime.h>
 
 #include "eat_launch.h"
@@ -208,7 +210,11 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
         const int64_t off = qa.arr_off ? __ldg(qa.arr_off + q) : (int64_t)q * V;
         int32_t *const out = qa.arr_out + off;
         const bool arr_shared = ARR == kArrShared || (ARR == kArrPerQuery && V <= qa.smem_arr_cap);
-        int32_t *const arr = arr_shared ? smem : out;
+        // Arrivals: shared memory, else the block's scratch row (when the output is
+        // host memory), else the output row itself.
+        int32_t *const arr = arr_shared ? smem
+                             : qa.arr_rows ? qa.arr_rows + (int64_t)blockIdx.x * qa.arr_rows_stride
+                                           : out;
         const int32_t nwords = (V + 31) >> 5;
         uint32_t *const mask0 = mask_base;
         uint32_t *const mask1 = mask_base + qa.mask_words;
@@ -337,9 +343,9 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
         }
         const int32_t F = n_items + n_spill;
 
-        if (arr_shared) {
+        if (arr_shared || qa.arr_rows) {
             __syncthreads();
-            for (int32_t i = tid; i < V; i += nthr) out[i] = arr[i];
+            for (int32_t i = tid; i < V; i += nthr) out[i] = load_arr(arr, i, arr_shared);
         }
         if (tid == 0 && qa.status)
             qa.status[q] = !valid ? EAT_ERR_INVALID : (F > 0 ? EAT_ERR_NO_CONVERGENCE : EAT_OK);
@@ -420,7 +426,11 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
         const int64_t off = qa.arr_off ? __ldg(qa.arr_off + q) : (int64_t)q * V;
         int32_t *const out = qa.arr_out + off;
         const bool arr_shared = ARR == kArrShared || (ARR == kArrPerQuery && V <= qa.smem_arr_cap);
-        int32_t *const arr = arr_shared ? smem : out;
+        // Arrivals: shared memory, else the block's scratch row (when the output is
+        // host memory), else the output row itself.
+        int32_t *const arr = arr_shared ? smem
+                             : qa.arr_rows ? qa.arr_rows + (int64_t)blockIdx.x * qa.arr_rows_stride
+                                           : out;
         const int32_t nwords = (V + 31) >> 5;
         const int32_t nchunks = (nwords + 31) >> 5;
 
@@ -540,8 +550,8 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
         }
         __syncthreads();
 
-        if (arr_shared)
-            for (int32_t i = tid; i < V; i += nthr) out[i] = arr[i];
+        if (arr_shared || qa.arr_rows)
+            for (int32_t i = tid; i < V; i += nthr) out[i] = load_arr(arr, i, arr_shared);
         if (tid == 0 && qa.status)
             qa.status[q] = !valid ? EAT_ERR_INVALID : (s_err ? EAT_ERR_NO_CONVERGENCE : EAT_OK);
         if (qa.counters) {

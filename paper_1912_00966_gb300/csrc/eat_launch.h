@@ -30,6 +30,9 @@ struct QueryArgs {
     int32_t smem_mask_off;     // int offset of the bitmaps in dynamic shared memory
     int32_t smem_q_off;        // int offset of the item buffers in dynamic shared memory
     int32_t smem_arr_cap;      // per-query placement: arrivals shared when n_stops <= this
+    int32_t *arr_rows;         // [grid][arr_rows_stride]: a block's arrivals when they are not
+                               // in shared memory and arr_out is host memory, or nullptr
+    int64_t arr_rows_stride;   // ints per block row
 };
 
 // mem: 0 = arrivals and bitmaps in shared memory, 1 = arrivals global / bitmaps
