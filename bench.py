@@ -50,10 +50,12 @@ FALLBACK_HBM_GBS = 6800.0
 # initialisation + 4 B x V result row.
 BYTES = {"vertices": 20, "types": 16, "evals": 4, "lookups": 8, "aps": 16, "relaxed": 12}
 
-# DRAM bytes per query of the CTA kernel on the city workload, from the ncu capture
-# summarised in profiles/; keyed by the kernel source hash so that a changed kernel
-# reports null until it is profiled again.
-NCU_TRAFFIC_PER_QUERY = {"city": ("2fdb761e654e087d", 75679232 / 256)}
+# DRAM bytes per query of the CTA kernel, from the ncu captures summarised in profiles/
+# (city: one 256-query launch; large: one 152-query launch, one query per SM, taken as
+# the per-query traffic of the 1,024-query step too); keyed by the kernel source hash
+# so that a changed kernel reports null until it is profiled again.
+NCU_TRAFFIC_PER_QUERY = {"city": ("d85bd334bda56a3b", 75849728 / 256),
+                         "large": ("d85bd334bda56a3b", 6414423512 / 152)}
 
 
 def kernel_hash() -> str:
@@ -437,11 +439,28 @@ def cpu_oracle_rate(tt, batches, budget_s, threads):
     return done / t_used, used, done, t_used
 
 
+def cpu_oracle_latency(tt, src, ts, budget_s, max_q=64):
+    """The oracle one query at a time on one thread (the paper's serial baseline)."""
+    import oracle
+    sc = oracle.SortedConnections(tt)
+    oracle.csa(sc, int(src[0]), int(ts[0]))
+    done, t_used = 0, 0.0
+    for i in range(min(max_q, len(src))):
+        t0 = time.perf_counter()
+        oracle.csa(sc, int(src[i]), int(ts[i]))
+        t_used += time.perf_counter() - t0
+        done += 1
+        if t_used >= budget_s:
+            break
+    return 1e3 * t_used / done, done
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
     tt, batch = workload(args.workload)
+    batch = args.batch or batch
     batches = [(q.source, q.t_s) for q in
                (synth.random_queries(tt, batch, 0xB0 + i) for i in range(args.warmup + args.steps))]
     import oracle
@@ -484,6 +503,7 @@ def run_ours(args):
     from paper_1912_00966_gb300 import eat
 
     tt, batch = workload(args.workload)
+    batch = args.batch or batch
     t_build = time.perf_counter()
     net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=dev, trip=tt.trip,
                         subtrips=args.subtrips, cluster_width=args.cluster_width)
@@ -614,12 +634,26 @@ def run_ours(args):
         threads = os.cpu_count() or 1
         rate, used, done, spent = cpu_oracle_rate(
             tt, [(q.source, q.t_s) for q in qsets[args.warmup:]], args.cpu_budget, threads)
+        lat_ms, lat_n = cpu_oracle_latency(tt, qsets[args.warmup].source,
+                                           qsets[args.warmup].t_s, 2.0)
         cpu = {"value": rate, "unit": "queries/s", "cores": used, "kind": "oracle",
                "sample": f"{done} of the timed steps' queries ({done // batch} whole "
                          f"{batch}-query batches), connection scan on {used} threads, "
-                         f"{spent:.1f} s"}
+                         f"{spent:.1f} s",
+               "single_thread_ms_per_query": lat_ms,
+               "single_thread_sample": f"first {lat_n} queries of the first timed step, "
+                                       "one at a time on one thread"}
 
     n_q = batch * args.steps * world
+    # Connections the connection scan would examine for the same queries (those
+    # departing at or after t_s), per second of GPU time.
+    dep_sorted = np.sort(tt.dep)
+    csa_conn = 0
+    for q in qsets[args.warmup:]:
+        first = np.searchsorted(dep_sorted, q.t_s, side="left").astype(np.int64)
+        csa_conn += int((len(dep_sorted) - first).sum())
+    # Mean rounds per query of the timed batches (0 in the round-free mode).
+    rounds_mean = tot["rounds"] / (batch * args.steps)
     line = {
         "metric": "EAT queries/s (batched)",
         "value": n_q / gpu_s,
@@ -642,6 +676,7 @@ def run_ours(args):
                      "kernel": kernel_name, "alg_bytes_per_launch": per_launch},
         "cpu_baseline": cpu,
         "connections_relaxed_per_s": tot["types"] / (gpu_s / world),
+        "csa_equivalent_connections_per_s": csa_conn / (gpu_s / world),
         "subtrips": {0: "none", 1: "sqrt(k) per trip", 2: "sqrt(mean trip length)"}[args.subtrips],
         "cluster_width_s": args.cluster_width,
         "launch_shape": tuned if tuned else {"block": args.block, "vwarp": args.vwarp,
@@ -650,7 +685,10 @@ def run_ours(args):
             {"value": batch / (base_ms / 1e3), "unit": "queries/s", "ms_per_step": base_ms},
         "build_s": t_build,
         "plain_single_query": {"value": plain_n / plain_s, "unit": "queries/s",
-                               "ms_per_query": 1e3 * plain_s / plain_n},
+                               "ms_per_query": 1e3 * plain_s / plain_n,
+                               "rounds_mean": rounds_mean,
+                               "us_per_round": (1e6 * plain_s / plain_n / rounds_mean
+                                                if rounds_mean else None)},
         "work_per_query": {n: tot[n] / (batch * args.steps) for n in names},
         "network": {k: st[k] for k in ("n_types", "n_edges", "n_ap", "n_cl", "max_clusters",
                                        "device_bytes", "n_shortcuts", "y")},
@@ -686,6 +724,8 @@ def main():
     ap.add_argument("--subtrips", type=int, default=0, choices=[0, 1, 2],
                     help="sub-trip shortcuts (Section III-G): 0 none, 1 sqrt(k), 2 sqrt(mean)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="queries per step (default: the workload's: 256, or 1,024 for large)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

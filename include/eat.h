@@ -356,20 +356,21 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
 /*
  * eat_autotune -- choose the launch shape for this network by measurement (no
  * counterpart in the paper, which fixes one thread per type or per edge and
- * sweeps the virtual-warp size by hand, Section V-B).  Candidates: every block
- * size (256, 512, 1024 threads) with the round-based mode and every vwarp (2,
- * 4, 8, 16, 32 lanes per spilled stop), and each block size with the
- * asynchronous mode, as far as they fit the device.  They are run on the sample
- * batch sources/times (n queries, device memory) in five rounds over all
- * candidates: the first warms up, the other four are timed with CUDA events on
- * `stream`, each after a write of twice the L2 size so that every timing starts
- * with the network out of cache.  The shape with the least median time is
- * stored for batches of about n queries in the network; afterwards every query
- * call that leaves opts->block, opts->vwarp and opts->mode at 0 uses it (a call
- * with a round cap keeps the round-based mode).  The tuned shape is written to
- * *best (may be NULL).  Blocks until done.  Allocates its own scratch
- * (workspace, output rows and the cache-flush buffer) for the duration of the
- * call.  Errors: as eat_query_batch; EAT_ERR_INVALID if no shape fits.
+ * sweeps the virtual-warp size by hand, Section V-B).  Candidates, in this
+ * order: block sizes 512, 1024 and 256 threads, each with the round-based mode
+ * and vwarp 8, 4, 16, 2, 32 lanes per spilled stop, then with the asynchronous
+ * mode, as far as they fit the device.  They are run on the sample batch
+ * sources/times (n queries, device memory) in five rounds over all candidates:
+ * the first warms up, the other four are timed with CUDA events on `stream`,
+ * each after a write of twice the L2 size so that every timing starts with the
+ * network out of cache.  The earliest candidate whose median time is within 2 %
+ * of the least median wins (closer differences are within timing noise), and
+ * is stored for batches of about n queries in the network; afterwards every
+ * query call that leaves opts->block, opts->vwarp and opts->mode at 0 uses it
+ * (a call with a round cap keeps the round-based mode).  The tuned shape is
+ * written to *best (may be NULL).  Blocks until done.  Allocates its own
+ * scratch (workspace, output rows and the cache-flush buffer) for the duration
+ * of the call.  Errors: as eat_query_batch; EAT_ERR_INVALID if no shape fits.
  */
 int eat_autotune(eat_net *net, const int32_t *sources, const int32_t *times, int32_t n,
                  eat_query_opts *best, void *stream);

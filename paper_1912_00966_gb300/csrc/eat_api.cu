@@ -828,8 +828,10 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
         std::vector<float> ms;
     };
     std::vector<Cand> cands;
-    for (int b : {256, 512, 1024}) {
-        for (int v : {2, 4, 8, 16, 32}) cands.push_back({EAT_MODE_CTA, b, v, {}});
+    // Fixed order, the library default (512 threads, vwarp 8, rounds) first: ties
+    // below go to the earliest.
+    for (int b : {512, 1024, 256}) {
+        for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, {}});
         eat_query_opts o{};
         o.block = b;
         o.vwarp = 8;
@@ -901,17 +903,23 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
             }
         }
     }
-    int best_b = 512, best_v = 8, best_m = EAT_MODE_CTA;
-    float best_ms = 1e30f;
+    // Least median time; shapes within 2 % of it count as tied (the spread of repeated
+    // timings of one shape), and a tie goes to the earliest candidate in the fixed
+    // order above, so that repeated tuning of one network settles on one shape.
+    float least = 1e30f;
     for (Cand &cd : cands) {
         if (cd.ms.size() != (size_t)kTimed) continue;
         std::sort(cd.ms.begin(), cd.ms.end());
-        const float med = 0.5f * (cd.ms[kTimed / 2 - 1] + cd.ms[kTimed / 2]);
-        if (med < best_ms) {
-            best_ms = med;
+        cd.ms[0] = 0.5f * (cd.ms[kTimed / 2 - 1] + cd.ms[kTimed / 2]);   // median
+        least = std::min(least, cd.ms[0]);
+    }
+    int best_b = 512, best_v = 8, best_m = EAT_MODE_CTA;
+    for (const Cand &cd : cands) {
+        if (cd.ms.size() == (size_t)kTimed && cd.ms[0] <= least * 1.02f) {
             best_b = cd.b;
             best_v = cd.v;
             best_m = cd.m;
+            break;
         }
     }
     if (e0) cudaEventDestroy(e0);
