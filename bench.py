@@ -59,8 +59,11 @@ NCU_TRAFFIC_PER_QUERY = {"city": ("d85bd334bda56a3b", 75849728 / 256),
 
 
 def kernel_hash() -> str:
-    p = os.path.join(ROOT, "paper_1912_00966_gb300", "csrc", "eat_kernels.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Hash of the sources the query kernels compile from."""
+    h = hashlib.sha256()
+    for f in ("eat_kernels.cu", "eat_device.cuh", "eat_launch.h", "eat_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1912_00966_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 RAGGED_QUERIES = 4096
@@ -455,6 +458,92 @@ def cpu_oracle_latency(tt, src, ts, budget_s, max_q=64):
     return 1e3 * t_used / done, done
 
 
+LADDER_NAMES = {1: "Connection (Algorithm 4)", 2: "Connection-Type (Algorithm 5)",
+                3: "Connection-Type-AP (Algorithm 6)", 4: "Cluster-AP (Section III-D)",
+                5: "Edge (Section III-E)", 6: "Warps (Section III-F)"}
+
+
+def run_ladder(args):
+    """Single-query latency of the paper's topology-driven variants (Table II's ladder, on
+    the synthetic city network), with the flag read after every round and every
+    ceil(sqrt(d)) rounds (Section V-D), beside the frontier-driven kernel and the oracle."""
+    import torch
+    from paper_1912_00966_gb300 import eat
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    tt = synth.city()
+    V = tt.n_stops
+    n_q = args.batch or 16
+    qs = synth.random_queries(tt, n_q, 0xB0)
+    t0 = time.perf_counter()
+    lad = eat.eat_ladder_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur,
+                               cluster_width=args.cluster_width, device=0)
+    t_build = time.perf_counter() - t0
+    net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=0,
+                        cluster_width=args.cluster_width)
+    out = torch.empty(V, dtype=torch.int32, device="cuda")
+    pairs = [(int(qs.source[i]), int(qs.t_s[i])) for i in range(n_q)]
+    # Temporal depth of the sample: rounds with a flag read after every round, minus the
+    # last round that finds nothing.
+    depth = 0
+    for s_, t_ in pairs:
+        _, st = eat.eat_ladder_query(lad, eat.EAT_VAR_CLUSTER_AP, s_, t_, out=out, flag_every=1)
+        depth = max(depth, st["rounds"] - 1)
+    every_sqrt = max(1, int(np.ceil(np.sqrt(depth))))
+
+    def timed(fn):
+        fn(*pairs[0])
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        extra = [fn(s_, t_) for s_, t_ in pairs]
+        return 1e3 * (time.perf_counter() - t) / n_q, extra
+
+    rows = []
+    with ClockSampler(0) as clocks:
+        clocks.wait_first()
+        clocks.mark()
+        for v in range(1, 7):
+            for every in (1, every_sqrt):
+                ms, st = timed(lambda s_, t_: eat.eat_ladder_query(lad, v, s_, t_, out=out,
+                                                                   flag_every=every)[1])
+                rows.append({"variant": LADDER_NAMES[v], "flag_every": every, "ms_per_query": ms,
+                             "rounds_mean": float(np.mean([x["rounds"] for x in st])),
+                             "flag_reads_mean": float(np.mean([x["flag_reads"] for x in st]))})
+        ms_front, _ = timed(lambda s_, t_: eat.eat_query(net, s_, t_, out))
+        src_d = torch.as_tensor(qs.source).cuda()
+        ts_d = torch.as_tensor(qs.t_s).cuda()
+        rows_d = torch.empty(n_q * V, dtype=torch.int32, device="cuda")
+        eat.eat_query_batch(net, src_d, ts_d, rows_d)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        eat.eat_query_batch(net, src_d, ts_d, rows_d)
+        torch.cuda.synchronize()
+        ms_batch = 1e3 * (time.perf_counter() - t) / n_q
+        clocks.stop_mark()
+    cpu_ms = None
+    if not args.no_cpu_baseline:
+        cpu_ms, _ = cpu_oracle_latency(tt, qs.source, qs.t_s, 10.0, max_q=n_q)
+    for r in rows:
+        r["speedup_vs_oracle_single_thread"] = None if cpu_ms is None else cpu_ms / r["ms_per_query"]
+    line = {
+        "metric": "EAT single-query latency by variant (the ladder of Section III, Table II)",
+        "unit": "ms/query", "n_gpus": 1, "higher_is_better": False, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": describe("city", tt, n_q)["workload"], "queries": n_q,
+                   "cluster_width_s": args.cluster_width, "temporal_depth_of_sample": depth,
+                   "timing": "host wall clock around each blocking call; L2 not flushed"},
+        "variants": rows,
+        "frontier_kernel": {"eat_query_ms": ms_front, "eat_query_batch_ms_per_query": ms_batch},
+        "oracle_single_thread_ms_per_query": cpu_ms,
+        "ladder_build_s": t_build,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line))
+    lad.close()
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -707,7 +796,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="city",
-                    choices=["city", "small", "large", "ragged", "serve"])
+                    choices=["city", "small", "large", "ragged", "serve", "ladder"])
     ap.add_argument("--serve-rates", type=int, nargs="+", default=[1000, 5000, 20000, 50000])
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-batch", type=int, default=256)
@@ -735,6 +824,8 @@ def main():
         return run_ours_ragged(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "ladder":
+        return run_ladder(args)
     return run_ours(args)
 
 

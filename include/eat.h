@@ -473,6 +473,80 @@ int eat_query_batch_noalloc(const eat_net *net, const int32_t *sources, const in
                             int32_t n, int32_t *arr_out, const eat_query_opts *opts,
                             void *stream);
 
+/* ------------------------------------------------------------------------
+ * Topology-driven variants (Section III-A to III-F), the paper's own execution
+ * model, kept as a baseline and to show what each pruning step buys.
+ *
+ * One query at a time.  Each round one kernel visits every connection, type or
+ * edge and works only on those whose tail stop is active, i.e. was improved in
+ * the round before (Section IV-B's active / nextactive pair, kept here as two
+ * arrays of round stamps).  The host drives the rounds and reads the device's
+ * "improved in round i" flag every `flag_every` rounds (Section V-D: 1 = after
+ * every round, as in Algorithms 4-5; about sqrt(d) = the reduced transfer of
+ * Table V); the rounds run after convergence find nothing active.
+ * ------------------------------------------------------------------------ */
+typedef struct eat_ladder eat_ladder;
+
+enum eat_variant {
+    EAT_VAR_CONNECTION = 1,   /* Algorithm 4: one thread per connection; relax if its
+                                 tail is active and e[u] <= t */
+    EAT_VAR_TYPE = 2,         /* Algorithm 5: one thread per connection type; the
+                                 earliest departure >= e[u] by linear search of the
+                                 type's sorted departures (getConnection) */
+    EAT_VAR_TYPE_AP = 3,      /* Section III-C: as 2, the departure from the type's
+                                 whole-day AP tuples (Algorithm 6) */
+    EAT_VAR_CLUSTER_AP = 4,   /* Section III-D: as 3 inside the cluster of e[u], else
+                                 the next non-empty cluster's first departure */
+    EAT_VAR_EDGE = 5,         /* Section III-E: one thread per edge (u, v), all its
+                                 types by Cluster-AP */
+    EAT_VAR_WARP = 6          /* Section III-F: one warp per edge, its types spread
+                                 over the lanes, by Cluster-AP */
+};
+
+typedef struct {
+    int32_t rounds;       /* rounds launched (including those after convergence) */
+    int32_t flag_reads;   /* device-to-host copies of the flag */
+} eat_ladder_stats;
+
+/*
+ * eat_ladder_build -- everything the variants read, on opts->device (>= 0):
+ * the Cluster-AP network of eat_build (same options and errors) plus the
+ * connections themselves (16 B each), every type's {tail, head, duration},
+ * its sorted unique departures and its whole-day greedy AP cover (the cover
+ * rule of Section II, as in the clusters, over all of the type's departures:
+ * first term, difference and terms as int32), and the edges (runs of types
+ * with the same tail and head).  Input arrays are copied.  Free with
+ * eat_ladder_free.  Errors: as eat_build; EAT_ERR_NO_DEVICE for device < 0.
+ */
+int eat_ladder_build(const eat_connections *conn, const eat_build_opts *opts,
+                     eat_ladder **out);
+void eat_ladder_free(eat_ladder *l);
+
+/*
+ * eat_ladder_query -- one query (s, t_s) with `variant` (enum eat_variant),
+ * blocking.  arr_out: [n_stops] int32, host or device memory, as eat_query.
+ * flag_every >= 1: rounds between flag reads.  stats may be NULL.  Calls on
+ * one ladder are serialised internally.
+ * Errors: EAT_ERR_INVALID (bad variant, s out of range, flag_every < 1),
+ * EAT_ERR_NO_CONVERGENCE (more than n_stops + flag_every rounds), EAT_ERR_CUDA.
+ */
+int eat_ladder_query(eat_ladder *l, int32_t variant, int32_t s, int32_t t_s, int32_t flag_every,
+                     int32_t *arr_out, eat_ladder_stats *stats);
+
+/*
+ * eat_ladder_host_view -- the variants' host copies, valid until
+ * eat_ladder_free: per type t, tail/head/duration at type_uvl[3t .. 3t+2];
+ * departures dep[dep_ptr[t] .. dep_ptr[t+1]); whole-day APs
+ * ap[3a .. 3a+2] = {first, difference, terms} for a in [ap_ptr[t], ap_ptr[t+1]);
+ * edge e = types [edge_ptr[e], edge_ptr[e+1]).
+ */
+typedef struct {
+    int32_t n_types, n_edges;
+    int64_t n_dep, n_ap;
+    const int32_t *type_uvl, *dep_ptr, *dep, *ap_ptr, *ap, *edge_ptr;
+} eat_ladder_view;
+int eat_ladder_host_view(const eat_ladder *l, eat_ladder_view *view);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,9 +18,9 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["eat_kernels.cu", "eat_api.cu", "eat_server.cu"]
+CU_SOURCES = ["eat_kernels.cu", "eat_api.cu", "eat_server.cu", "eat_ladder.cu"]
 CPP_SOURCES = ["eat_build.cpp"]
-HEADERS = ["eat_internal.h", "eat_launch.h"]
+HEADERS = ["eat_internal.h", "eat_launch.h", "eat_device.cuh"]
 
 
 def _sources():

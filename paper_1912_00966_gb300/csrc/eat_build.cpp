@@ -103,22 +103,23 @@ void build_chunk(Chunk &ch, const std::vector<int64_t> &u_off, std::vector<Rec> 
 
 }  // namespace
 
-// Greedy AP cover of one cluster (Section II, Arithmetic Progression Technique):
-// repeatedly take the smallest uncovered value a; among the APs a, a+d, a+2d, ...
-// that stay inside the set (one per later value, i.e. per difference d, each
-// extended as far as it goes) take the one covering the most uncovered values,
-// then the longest, then the smallest d.  Values are sorted and unique and span
-// less than `width_hint` seconds.  APs come out in increasing first term.
-void ap_cover(const int32_t *d, int32_t n, int32_t width_hint, std::vector<uint32_t> &out) {
+namespace {
+
+// Greedy AP cover (Section II, Arithmetic Progression Technique): repeatedly take
+// the smallest uncovered value a; among the APs a, a+d, a+2d, ... that stay inside
+// the set (one per later value, i.e. per difference d, each extended as far as it
+// goes) take the one covering the most uncovered values, then the longest, then
+// the smallest d.  Values are sorted and unique.  Calls emit(first, d, terms) per
+// AP in increasing first term (d = 0 for a one-term AP).
+template <class Emit>
+void ap_cover_core(const int32_t *d, int32_t n, Emit emit) {
     if (n == 1) {
-        out.push_back((uint32_t)d[0]);
-        out.push_back(1u);
+        emit(d[0], 0, 1);
         return;
     }
     const int32_t base = d[0];
     const int32_t top = d[n - 1];
     const int32_t span = top - base + 1;
-    (void)width_hint;
     Bits &bits = tl_bits;
     bits.ensure((size_t)span);
     for (int32_t i = 0; i < n; ++i) Bits::set(bits.present, d[i] - base);
@@ -149,12 +150,33 @@ void ap_cover(const int32_t *d, int32_t n, int32_t width_hint, std::vector<uint3
                 ++n_cov;
             }
         }
-        out.push_back((uint32_t)a);
-        out.push_back(((uint32_t)best_step << 16) | (uint32_t)best_len);
+        emit(a, best_step, best_len);
     }
     const size_t words = ((size_t)span + 63) / 64;
     std::memset(bits.present.data(), 0, words * sizeof(uint64_t));
     std::memset(bits.covered.data(), 0, words * sizeof(uint64_t));
+}
+
+}  // namespace
+
+// Greedy AP cover of one cluster (values span less than `width_hint` < 2^16
+// seconds): appends {first, difference << 16 | terms} per AP.
+void ap_cover(const int32_t *d, int32_t n, int32_t width_hint, std::vector<uint32_t> &out) {
+    (void)width_hint;
+    ap_cover_core(d, n, [&](int32_t a, int32_t step, int32_t len) {
+        out.push_back((uint32_t)a);
+        out.push_back(((uint32_t)step << 16) | (uint32_t)len);
+    });
+}
+
+// Greedy AP cover of any sorted unique values (e.g. a connection type's whole
+// day): appends {first, difference, terms} per AP.
+void ap_cover_wide(const int32_t *d, int32_t n, std::vector<int32_t> &out) {
+    ap_cover_core(d, n, [&](int32_t a, int32_t step, int32_t len) {
+        out.push_back(a);
+        out.push_back(step);
+        out.push_back(len);
+    });
 }
 
 int build_host(const eat_connections *c, int32_t width, int32_t t0, HostNet &h) {

@@ -114,4 +114,8 @@ int build_fused(HostNet &h);
 void ap_cover(const int32_t *vals, int32_t n, int32_t width_hint,
               std::vector<uint32_t> &out_ap);
 
+// Greedy AP cover of any sorted unique values (eat_build.cpp); appends
+// (first, difference, terms) as three int32 per AP.
+void ap_cover_wide(const int32_t *vals, int32_t n, std::vector<int32_t> &out);
+
 }  // namespace eat

@@ -22,6 +22,8 @@ EAT_MODE_AUTO, EAT_MODE_CTA, EAT_MODE_GRID, EAT_MODE_ASYNC = 0, 1, 2, 3
 EAT_PLACE_AUTO, EAT_PLACE_SHARED, EAT_PLACE_GLOBAL_ARR, EAT_PLACE_GLOBAL = 0, 1, 2, 3
 EAT_SUBTRIPS_NONE, EAT_SUBTRIPS_SQRT_K, EAT_SUBTRIPS_SQRT_MEAN = 0, 1, 2
 EAT_MAX_NETS = 128
+EAT_VAR_CONNECTION, EAT_VAR_TYPE, EAT_VAR_TYPE_AP = 1, 2, 3
+EAT_VAR_CLUSTER_AP, EAT_VAR_EDGE, EAT_VAR_WARP = 4, 5, 6
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libeat.so not found at {LIB_PATH}: build it with "
@@ -138,10 +140,30 @@ _sig("eat_server_poll", ctypes.c_int32, [_vp, ctypes.POINTER(eat_server_result),
 _sig("eat_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(eat_server_stats)])
 _sig("eat_server_destroy", None, [_vp])
 
+
+class eat_ladder_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("flag_reads", ctypes.c_int32)]
+
+
+class eat_ladder_view(ctypes.Structure):
+    _fields_ = [("n_types", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("n_dep", ctypes.c_int64), ("n_ap", ctypes.c_int64),
+                ("type_uvl", _vp), ("dep_ptr", _vp), ("dep", _vp), ("ap_ptr", _vp), ("ap", _vp),
+                ("edge_ptr", _vp)]
+
+
+_sig("eat_ladder_build", ctypes.c_int, [ctypes.POINTER(eat_connections),
+                                        ctypes.POINTER(eat_build_opts), ctypes.POINTER(_vp)])
+_sig("eat_ladder_free", None, [_vp])
+_sig("eat_ladder_query", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, _vp, ctypes.POINTER(eat_ladder_stats)])
+_sig("eat_ladder_host_view", ctypes.c_int, [_vp, ctypes.POINTER(eat_ladder_view)])
+
 EXPORTED = ("eat_autotune", "eat_server_create", "eat_server_submit", "eat_server_poll", "eat_server_get_stats",
             "eat_server_destroy", "eat_last_error", "eat_version", "eat_build", "eat_build_csr", "eat_free", "eat_get_stats",
             "eat_net_host_view", "eat_query", "eat_workspace_bytes", "eat_query_batch",
-            "eat_query_batch_multi", "eat_next_departure", "eat_query_batch_noalloc")
+            "eat_query_batch_multi", "eat_next_departure", "eat_query_batch_noalloc",
+            "eat_ladder_build", "eat_ladder_free", "eat_ladder_query", "eat_ladder_host_view")
 
 
 class EatError(RuntimeError):
@@ -408,3 +430,71 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Ladder:
+    """Owning handle of an eat_ladder (released by eat_ladder_free)."""
+
+    def __init__(self, handle):
+        self._h = _vp(handle)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("ladder already freed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.eat_ladder_free(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def eat_ladder_build(n_stops, u, v, dep, dur, cluster_width=0, t0=0, device=0) -> Ladder:
+    """The topology-driven variants' arrays (see eat.h); device=-1 builds host arrays only."""
+    u, v, dep, dur = _i32(u), _i32(v), _i32(dep), _i32(dur)
+    n = u.shape[0]
+    if not (v.shape[0] == dep.shape[0] == dur.shape[0] == n):
+        raise ValueError("connection arrays differ in length")
+    c = eat_connections(int(n_stops), int(n), u.ctypes.data, v.ctypes.data, dep.ctypes.data,
+                        dur.ctypes.data, None)
+    o = eat_build_opts(int(cluster_width), int(t0), int(device), 0)
+    h = _vp()
+    _check(_lib.eat_ladder_build(ctypes.byref(c), ctypes.byref(o), ctypes.byref(h)),
+           "eat_ladder_build")
+    return Ladder(h.value)
+
+
+def eat_ladder_query(ladder: Ladder, variant, s, t_s, out=None, flag_every=1, n_stops=None):
+    """One blocking query with a topology-driven variant; returns (out, stats dict)."""
+    if out is None:
+        if n_stops is None:
+            raise ValueError("pass `out` or `n_stops`")
+        out = np.empty(int(n_stops), dtype=np.int32)
+    st = eat_ladder_stats()
+    _check(_lib.eat_ladder_query(ladder.handle, int(variant), int(s), int(t_s), int(flag_every),
+                                 _ptr(out), ctypes.byref(st)), "eat_ladder_query")
+    return out, {"rounds": st.rounds, "flag_reads": st.flag_reads}
+
+
+def eat_ladder_host_view(ladder: Ladder) -> dict:
+    """Copies of the variants' host arrays: type_uvl [T, 3], dep_ptr, dep, ap_ptr, ap [A, 3],
+    edge_ptr."""
+    vw = eat_ladder_view()
+    _check(_lib.eat_ladder_host_view(ladder.handle, ctypes.byref(vw)), "eat_ladder_host_view")
+    T, E = vw.n_types, vw.n_edges
+
+    def arr(p, n):
+        if n == 0:
+            return np.zeros(0, dtype=np.int32)
+        return np.ctypeslib.as_array(ctypes.cast(p, _i32p), shape=(n,)).copy()
+
+    return {"type_uvl": arr(vw.type_uvl, 3 * T).reshape(T, 3), "dep_ptr": arr(vw.dep_ptr, T + 1),
+            "dep": arr(vw.dep, vw.n_dep), "ap_ptr": arr(vw.ap_ptr, T + 1),
+            "ap": arr(vw.ap, 3 * vw.n_ap).reshape(-1, 3), "edge_ptr": arr(vw.edge_ptr, E + 1)}
