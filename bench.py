@@ -87,7 +87,7 @@ def run_ours_ragged(args):
     t_build = time.perf_counter() - t_build
     n_steps = args.warmup + args.steps
     Q = RAGGED_QUERIES
-    qsets = [synth.random_queries(tts, Q, 0xA0 + 1000 * rank + i) for i in range(n_steps)]
+    qsets = rank_query_sets(tts, Q, n_steps, rank, 0xA0)
     Vs = np.array([t.n_stops for t in tts], np.int64)
     offs = [np.concatenate([[0], np.cumsum(Vs[q.net])[:-1]]).astype(np.int64) for q in qsets]
     total = max(int(Vs[q.net].sum()) for q in qsets)
@@ -169,10 +169,7 @@ def run_ours_ragged(args):
         eat.eat_query(nets[j], int(q0.source[i]), int(q0.t_s[i]), rows[j])
     plain_s = time.perf_counter() - t0
 
-    times = torch.tensor([gpu_s, sum(e2e_t), plain_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    gpu_s, e2e_s, plain_s = times.tolist()
+    gpu_s, e2e_s, plain_s = max_over_ranks([gpu_s, sum(e2e_t), plain_s], world)
     if rank != 0:
         return 0
     peak, peak_kind = measured_peak()
@@ -419,6 +416,24 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def rank_query_sets(nets, batch, n_steps, rank, base_seed):
+    """This rank's query batches: every rank draws its own (weak scaling, replicas); the
+    seeds of different ranks never meet for fewer than 1,000 steps."""
+    return [synth.random_queries(nets, batch, base_seed + 1000 * rank + i) for i in range(n_steps)]
+
+
+def max_over_ranks(values, world):
+    """Element-wise maximum over ranks (the slowest replica sets the whole-job time)."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -600,7 +615,7 @@ def run_ours(args):
     st = eat.eat_get_stats(net)
     V = tt.n_stops
     n_steps = args.warmup + args.steps
-    qsets = [synth.random_queries(tt, batch, 0xB0 + 1000 * rank + i) for i in range(n_steps)]
+    qsets = rank_query_sets(tt, batch, n_steps, rank, 0xB0)
     src_d = [torch.as_tensor(q.source).cuda() for q in qsets]
     ts_d = [torch.as_tensor(q.t_s).cuda() for q in qsets]
     out = torch.empty(batch * V, dtype=torch.int32, device="cuda")
@@ -701,10 +716,7 @@ def run_ours(args):
         eat.eat_query(net, int(q0.source[i]), int(q0.t_s[i]), row)
     plain_s = time.perf_counter() - t0
 
-    times = torch.tensor([gpu_s, sum(e2e_t), plain_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    gpu_s, e2e_s, plain_s = times.tolist()
+    gpu_s, e2e_s, plain_s = max_over_ranks([gpu_s, sum(e2e_t), plain_s], world)
     if rank != 0:
         return 0
 
