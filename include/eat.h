@@ -360,10 +360,10 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
  * order: block sizes 512, 1024 and 256 threads, each with the round-based mode
  * and vwarp 8, 4, 16, 2, 32 lanes per spilled stop, then with the asynchronous
  * mode, as far as they fit the device.  They are run on the sample batch
- * sources/times (n queries, device memory) in five rounds over all candidates:
- * the first warms up, the other four are timed with CUDA events on `stream`,
+ * sources/times (n queries, device memory) in nine rounds over all candidates:
+ * the first warms up, the other eight are timed with CUDA events on `stream`,
  * each after a write of twice the L2 size so that every timing starts with the
- * network out of cache.  The earliest candidate whose median time is within 2 %
+ * network out of cache.  The earliest candidate whose median time is within 3 %
  * of the least median wins (closer differences are within timing noise), and
  * is stored for batches of about n queries in the network; afterwards every
  * query call that leaves opts->block, opts->vwarp and opts->mode at 0 uses it

@@ -872,7 +872,7 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
     }
     // Rounds over all candidates (so that slow drift of the clock affects all
     // alike): round 0 warms up, rounds 1..kTimed are timed.
-    constexpr int kTimed = 4;
+    constexpr int kTimed = 8;
     for (int rep = 0; rep <= kTimed && !rc; ++rep) {
         for (Cand &cd : cands) {
             eat_query_opts o{};
@@ -903,7 +903,7 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
             }
         }
     }
-    // Least median time; shapes within 2 % of it count as tied (the spread of repeated
+    // Least median time; shapes within 3 % of it count as tied (the spread of repeated
     // timings of one shape), and a tie goes to the earliest candidate in the fixed
     // order above, so that repeated tuning of one network settles on one shape.
     float least = 1e30f;
@@ -915,7 +915,7 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
     }
     int best_b = 512, best_v = 8, best_m = EAT_MODE_CTA;
     for (const Cand &cd : cands) {
-        if (cd.ms.size() == (size_t)kTimed && cd.ms[0] <= least * 1.02f) {
+        if (cd.ms.size() == (size_t)kTimed && cd.ms[0] <= least * 1.03f) {
             best_b = cd.b;
             best_v = cd.v;
             best_m = cd.m;
