@@ -160,12 +160,14 @@ typedef struct {
 typedef struct {
     int32_t max_rounds;      /* round cap; 0 = n_stops + 1 (always enough: every
                                 productive round fixes at least one more stop) */
-    int32_t block;           /* threads per CTA: 0 = automatic, else 64..1024, multiple of 32 */
+    int32_t block;           /* threads per CTA: 0 = automatic (the tuned shape, else 1024
+                                when the batch has at most one query per SM, else 512);
+                                else 64..1024, multiple of 32 */
     int32_t vwarp;           /* lanes per active stop (1, 2, 4, 8, 16 or 32); 0 = automatic */
     int32_t mode;            /* EAT_MODE_* */
     int32_t placement;       /* EAT_PLACE_*: where a query's arrivals and frontier
                                 bitmap live; 0 = automatic */
-    int32_t reserved;
+    int32_t cluster;         /* blocks per query in EAT_MODE_CLUSTER: 2, 4 or 8; 0 = 8 */
     int32_t *status;         /* optional [n] per-query eat_status, device memory */
     eat_counters *counters;  /* optional [n] per-query counters, device memory */
 } eat_query_opts;
@@ -181,7 +183,15 @@ enum eat_placement {
 enum eat_mode {
     EAT_MODE_AUTO = 0,  /* library picks */
     EAT_MODE_CTA = 1,   /* one thread block per query; rounds end at block barriers */
-    EAT_MODE_GRID = 2,  /* reserved: all SMs on each round of one query (not available) */
+    EAT_MODE_CLUSTER = 2, /* one thread-block cluster of 8 blocks (on 8 SMs) per query, on
+                           one network: the arrivals and frontier bitmaps are spread over
+                           the cluster's shared memory (distributed shared memory) and a
+                           round ends at a cluster barrier; arrivals up to about
+                           440,000 stops.  Never chosen automatically: on GB300 the
+                           distributed-shared-memory round trips and the cluster
+                           barrier cost more per round than the extra blocks save (a
+                           single city query 0.51-0.58 ms against 0.30 ms with one
+                           1,024-thread block).  Not with eat_query_batch_noalloc */
     EAT_MODE_ASYNC = 3  /* one thread block per query, no rounds: warps claim pending stops
                            from a bitmap and relax their types as soon as they appear;
                            needs the bitmap (n_stops bits) in shared memory; the round cap

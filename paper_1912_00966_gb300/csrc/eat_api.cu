@@ -93,7 +93,7 @@ static int device_info(int dev, DeviceInfo &out) {
         DeviceGuard guard(dev);
         for (int nets : {1, EAT_MAX_NETS})
             for (int mem = 0; mem < 4; ++mem)
-                for (const void *k : {cta_kernel(nets, mem), async_kernel(nets, mem)}) {
+                for (const void *k : {cta_kernel(nets, mem), async_kernel(nets, mem), cluster_kernel()}) {
                     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(d.smem_optin - d.reserve));
                     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -123,6 +123,7 @@ struct Plan {
     size_t off_spill = 0, off_mask = 0;
     int nets = 1;
     bool async = false;           // round-free kernel (EAT_MODE_ASYNC)
+    int cluster = 0;              // blocks per query in cluster mode (EAT_MODE_CLUSTER), else 0
 };
 
 static constexpr size_t kWsHeader = 256;   // work counter + internal status / counters
@@ -179,8 +180,67 @@ static int make_async_plan(int dev, const DeviceInfo &d, int32_t vmax, int32_t n
     return EAT_OK;
 }
 
+static constexpr int kCluster = 8;   // blocks per query in cluster mode (portable maximum)
+
+// Plan of the cluster kernel: one cluster of kCluster blocks per query, each block
+// holding every kCluster-th arrival and its bits of both bitmaps, plus its own item
+// queues; the rest of a block's shared memory goes to the queues.
+static int make_cluster_plan(int dev, const DeviceInfo &d, int32_t vmax, int32_t n,
+                             const eat_query_opts *o, Plan &p) {
+    const int C = (o && o->cluster) ? o->cluster : kCluster;
+    if (C != 2 && C != 4 && C != 8) return fail(EAT_ERR_INVALID, "cluster must be 2, 4 or 8");
+    p.cluster = C;
+    p.mem = 0;
+    p.async = false;
+    p.nets = 1;
+    const size_t slice = ((size_t)vmax + C - 1) / C;
+    p.mask_words = (int32_t)align_up((slice + 31) / 32, 4);
+    const size_t arr_bytes = align_up(slice, 4) * 4;
+    const size_t base = arr_bytes + 2 * (size_t)p.mask_words * 4;
+    const size_t limit = d.smem_optin - d.reserve;
+    const size_t qmin = 256;
+    if (base + kQueueEntryBytes * qmin > limit)
+        return fail(EAT_ERR_INVALID, "arrivals do not fit in the shared memory of one cluster");
+    size_t cap = std::min((limit - base) / kQueueEntryBytes, std::max((size_t)vmax, qmin));
+    if (cap >= 64) cap &= ~(size_t)31;
+    p.qcap = (int32_t)std::max(cap, qmin);
+    p.smem_mask_off = (int32_t)(arr_bytes / 4);
+    p.smem_q_off = p.smem_mask_off + 2 * p.mask_words;
+    p.smem = base + kQueueEntryBytes * (size_t)p.qcap;
+    p.grid = std::max(n, 1) * C;
+    p.spill_stride = (int64_t)align_up((size_t)vmax * 2, 64);
+    p.mask_stride = 0;
+    p.off_spill = kWsHeader;
+    p.off_mask = p.off_spill + (size_t)p.grid * (size_t)p.spill_stride * 4;
+    p.ws_bytes = p.off_mask;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3((unsigned)p.block);
+    cfg.dynamicSmemBytes = p.smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cudaError_t e;
+    {
+        DeviceGuard guard(dev);
+        e = cudaOccupancyMaxActiveClusters(&clusters, cluster_kernel(), &cfg);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EAT_ERR_INVALID, std::string("cluster launch not possible: ") + cudaGetErrorString(e));
+    }
+    if (clusters < 1) return fail(EAT_ERR_INVALID, "no cluster fits the device with this block size");
+    return EAT_OK;
+}
+
 static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_query_opts *o,
-                     Plan &p, int32_t vmin = -1, const eat_net *tuned = nullptr) {
+                     Plan &p, int32_t vmin = -1, const eat_net *tuned = nullptr,
+                     bool allow_cluster = true) {
     if (vmin < 0) vmin = vmax;
     DeviceInfo d;
     int rc = device_info(dev, d);
@@ -195,7 +255,10 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
         tv = tuned->tuned_vwarp[cls];
         tm = tuned->tuned_mode[cls];
     }
-    p.block = (o && o->block) ? o->block : (tb ? tb : 512);
+    // Default shape: with at most one query per SM each query gets a 1,024-thread
+    // block (measured faster for single queries and small batches); fuller batches
+    // run two 512-thread blocks per SM unless a tuned shape says otherwise.
+    p.block = (o && o->block) ? o->block : (tb ? tb : (n >= 1 && n <= d.sms ? 1024 : 512));
     if (p.block < 64 || p.block > 1024 || p.block % 32)
         return fail(EAT_ERR_INVALID, "block must be a multiple of 32 in 64..1024");
     int vw = (o && o->vwarp) ? o->vwarp : (tv ? tv : 8);
@@ -203,8 +266,15 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     while ((1 << l) < vw) ++l;
     if ((1 << l) != vw || vw > 32) return fail(EAT_ERR_INVALID, "vwarp must be 1, 2, 4, 8, 16 or 32");
     p.vw_log2 = l;
-    if (o && o->mode != EAT_MODE_AUTO && o->mode != EAT_MODE_CTA && o->mode != EAT_MODE_ASYNC)
-        return fail(EAT_ERR_INVALID, "mode must be EAT_MODE_AUTO, EAT_MODE_CTA or EAT_MODE_ASYNC");
+    if (o && (o->mode < EAT_MODE_AUTO || o->mode > EAT_MODE_ASYNC))
+        return fail(EAT_ERR_INVALID, "mode must be one of EAT_MODE_*");
+    if (o && o->mode == EAT_MODE_CLUSTER) {
+        if (n_nets != 1) return fail(EAT_ERR_INVALID, "cluster mode serves one network per launch");
+        if (o->placement != EAT_PLACE_AUTO && o->placement != EAT_PLACE_SHARED)
+            return fail(EAT_ERR_INVALID, "cluster mode keeps arrivals in shared memory");
+        if (!allow_cluster) return fail(EAT_ERR_INVALID, "cluster mode is not available here");
+        return make_cluster_plan(dev, d, vmax, n, o, p);
+    }
     const bool rounds_needed = o && o->max_rounds > 0;   // the round cap needs rounds
     if ((o && o->mode == EAT_MODE_ASYNC) ||
         (tm == EAT_MODE_ASYNC && !rounds_needed && (!o || o->mode == EAT_MODE_AUTO)))
@@ -366,8 +436,9 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     NetDev devs[EAT_MAX_NETS];
     for (int i = 0; i < n_nets; ++i) devs[i] = nets[i]->dev;
-    e = p.async ? launch_async(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st)
-                : launch_cta(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st);
+    e = p.cluster ? launch_cluster(devs[0], qa, p.cluster, p.grid, p.block, p.smem, st)
+        : p.async ? launch_async(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st)
+                  : launch_cta(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "query kernel launch");
     return EAT_OK;
 }
@@ -988,7 +1059,7 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     if (!is_device_ptr(sources) || !is_device_ptr(times) || !is_device_ptr(arr_out))
         return fail(EAT_ERR_INVALID, "sources, times and arr_out must be device memory");
     Plan p;
-    int rc = make_plan(net->device, net->host.n_stops, n, 1, opts, p, -1, net);
+    int rc = make_plan(net->device, net->host.n_stops, n, 1, opts, p, -1, net, false);
     if (rc) return rc;
     // Fewer persistent blocks so that their queue spill fits the fixed scratch.
     const size_t per_block = (size_t)p.spill_stride * 4 + (size_t)p.mask_stride * 4;

@@ -34,6 +34,7 @@
 // of uneven size); two frontier bitmaps (this round's pushes, last round's) in
 // shared memory when they fit (SMEM_MASK).  Arrivals not kept in the output row
 // are copied there when the query converges.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "eat_device.cuh"
@@ -473,6 +474,222 @@ __global__ void eat_next_departure_kernel(const NetDev N, const int32_t *types,
 
 // ------------------------------------------------------------------ launchers
 
+// ------------------------------------------------------------------ cluster mode
+//
+// One thread-block cluster of C blocks per query (grid = n * C; no persistent
+// loop), for single queries and small batches that would leave most SMs idle.
+// The arrivals and both frontier bitmaps are spread over the cluster's shared
+// memory: stop v lives in block v mod C at slot v / C, and every block reads and
+// lowers other blocks' entries through distributed shared memory.  Each block
+// keeps its own (stop, type) item queues and pushes into them.  A round ends at a
+// cluster barrier; after it every block sums all blocks' push counters, so all
+// blocks take the same loop decisions and pass the same barriers.
+
+template <int NETS>
+__global__ void __launch_bounds__(1024, 1)
+eat_cluster_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) int32_t smem[];
+    __shared__ int32_t s_items[3];    // items this block reserved per round (rotating)
+    __shared__ int32_t s_spill[3];    // stops this block spilled per round (rotating)
+    __shared__ unsigned long long s_cnt[6];
+
+    const int C = (int)cluster.num_blocks();
+    const int me = (int)cluster.block_rank();
+    const int q = blockIdx.x / C;                     // the same for the whole cluster
+    if (q >= qa.n) return;
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    const int vw = 1 << qa.vw_log2;
+    const int lane = tid & (vw - 1);
+    const int sub = tid >> qa.vw_log2;
+    const int nsub = nthr >> qa.vw_log2;
+    const int32_t icap = qa.qcap;
+
+    int32_t *const item_base = smem + qa.smem_q_off;
+    int32_t *const spill_base = qa.spill + (int64_t)blockIdx.x * qa.spill_stride;
+    uint32_t *const mask0 = (uint32_t *)(smem + qa.smem_mask_off);
+    uint32_t *const mask1 = mask0 + qa.mask_words;
+    int32_t *const arr = smem;                        // this block's slots
+
+    const NetDev &N = nets.net[0];
+    const int32_t V = N.n_stops;
+    const int32_t mine = me < V ? (V - me + C - 1) / C : 0;   // stops me, me + C, ...
+    const int32_t mwords = (mine + 31) >> 5;
+    int32_t *const out = qa.arr_out + (qa.arr_off ? __ldg(qa.arr_off + q) : (int64_t)q * V);
+    // Arrival slot and bitmap word of stop v, in the block that holds it.
+    auto arr_of = [&](int32_t v) { return cluster.map_shared_rank(arr + v / C, v % C); };
+    auto word_of = [&](uint32_t *m, int32_t v) {
+        return cluster.map_shared_rank(m + ((v / C) >> 5), v % C);
+    };
+    auto bit_of = [&](int32_t v) { return 1u << ((v / C) & 31); };
+
+    // Algorithm 2 on this block's slots.
+    if (tid < 6) s_cnt[tid] = 0;
+    for (int32_t i = tid; i < mine; i += nthr) arr[i] = kInf;
+    for (int32_t i = tid; i < mwords; i += nthr) {
+        mask0[i] = 0u;
+        mask1[i] = 0u;
+    }
+    if (tid < 3) {
+        s_items[tid] = 0;
+        s_spill[tid] = 0;
+    }
+    const int32_t s = __ldg(qa.src + q);
+    const int32_t t_s = __ldg(qa.ts + q);
+    const bool valid = (unsigned)s < (unsigned)V;
+    __syncthreads();
+    // The source is the frontier of "round -1" in the block that holds it.
+    if (tid == 0 && valid && s % C == me) {
+        arr[s / C] = t_s;
+        spill_base[qa.vmax] = s;
+        s_spill[2] = 1;
+    }
+    cluster.sync();
+
+    int32_t n_items = 0, n_spill = s_spill[2];
+    int32_t total = 0;
+    for (int r = 0; r < C; ++r) total += *(volatile int32_t *)cluster.map_shared_rank(&s_spill[2], r);
+    int32_t rounds = 0;
+    int cs = 0;
+    int32_t c_vert = 0, c_types = 0, c_evals = 0, c_lookups = 0, c_aps = 0, c_relax = 0;
+    while (total > 0 && rounds < qa.max_rounds) {
+        const int wr = rounds & 1, rd = wr ^ 1;
+        int32_t *const iu_rd = item_base + (2 * rd) * icap;
+        int32_t *const it_rd = iu_rd + icap;
+        int32_t *const iu_wr = item_base + (2 * wr) * icap;
+        int32_t *const it_wr = iu_wr + icap;
+        const int32_t *const sp_rd = spill_base + (int64_t)rd * qa.vmax;
+        int32_t *const sp_wr = spill_base + (int64_t)wr * qa.vmax;
+        uint32_t *const pmask = wr ? mask1 : mask0;    // stops pushed this round
+        uint32_t *const cmask = wr ? mask0 : mask1;    // stops pushed last round
+        if (tid == 0) {
+            const int nx = cs == 2 ? 0 : cs + 1;
+            s_items[nx] = 0;
+            s_spill[nx] = 0;
+        }
+
+        // Relax type t of tail u (Algorithm 3 with getConnection, Algorithm 6); on
+        // success v joins this block's next frontier as items or as a spilled stop.
+        auto relax = [&](int32_t e_u, int32_t k, int32_t t) {
+            ++c_types;
+            ++c_lookups;
+            int4 ca, cb;                                // cb = {x|n, v, lambda|d, row of v}
+            load_entry(N.ce + 2 * ((int64_t)t * N.y + k), ca, cb);
+            int32_t n, x;
+            entry_aps(cb, N.apx, n, x);
+            const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, k), e_u, N.apx, c_aps);
+            if (tc == kInf) return;                     // no departure left (Section IV-D)
+            ++c_evals;
+            const int32_t v = cb.y;
+            const int32_t cand = tc + (cb.z & 0xffffff);
+            int32_t *const ev = arr_of(v);
+            if (cand >= *(volatile int32_t *)ev) return;
+            const int32_t old = atomicMin(ev, cand);
+            if (cand >= old) return;
+            ++c_relax;
+            const int32_t row = cb.w;
+            int32_t d = (int32_t)((uint32_t)cb.z >> 24);  // types leaving v
+            if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - row;
+            if (d <= 0) return;
+            const uint32_t bit = bit_of(v);
+            if (atomicOr(word_of(pmask, v), bit) & bit) return;   // already queued
+            const int32_t base = atomicAdd(&s_items[cs], d);
+            if (base + d <= icap) {
+                iu_wr[base] = v | kFirstItem;
+                it_wr[base] = row;
+                for (int32_t j = 1; j < d; ++j) {
+                    iu_wr[base + j] = v;
+                    it_wr[base + j] = row + j;
+                }
+            } else {
+                for (int32_t j = base; j < icap; ++j) iu_wr[j] = kNullItem;
+                sp_wr[atomicAdd(&s_spill[cs], 1)] = v;
+            }
+        };
+
+        for (int32_t i = tid; i < n_items; i += nthr) {
+            const int32_t raw = iu_rd[i];
+            if (raw == kNullItem) continue;
+            const int32_t u = raw & 0x7fffffff;
+            if (raw < 0) {                              // first item of u
+                atomicAnd(word_of(cmask, u), ~bit_of(u));
+                ++c_vert;
+            }
+            const int32_t e_u = *(volatile int32_t *)arr_of(u);
+            const int32_t k = cluster_slot(N, e_u);
+            if (k >= N.y) {
+                ++c_types;
+                continue;
+            }
+            relax(e_u, k, it_rd[i]);
+        }
+        for (int32_t i = sub; i < n_spill; i += nsub) {
+            const int32_t u = __ldcg(sp_rd + i);
+            const int32_t beg = __ldg(N.row_ptr + u);
+            const int32_t end = __ldg(N.row_ptr + u + 1);
+            if (lane == 0) {
+                atomicAnd(word_of(cmask, u), ~bit_of(u));
+                ++c_vert;
+            }
+            const int32_t e_u = *(volatile int32_t *)arr_of(u);
+            const int32_t k = cluster_slot(N, e_u);
+            if (k >= N.y) {
+                if (lane == 0) c_types += end - beg;
+                continue;
+            }
+            for (int32_t t = beg + lane; t < end; t += vw) relax(e_u, k, t);
+        }
+        cluster.sync();
+        n_items = min(s_items[cs], icap);
+        n_spill = s_spill[cs];
+        total = 0;
+        for (int r = 0; r < C; ++r) {
+            total += min(*(volatile int32_t *)cluster.map_shared_rank(&s_items[cs], r), icap);
+            total += *(volatile int32_t *)cluster.map_shared_rank(&s_spill[cs], r);
+        }
+        cs = cs == 2 ? 0 : cs + 1;
+        ++rounds;
+    }
+
+    if (qa.counters) {
+        unsigned long long c[6] = {(unsigned long long)c_vert, (unsigned long long)c_types,
+                                   (unsigned long long)c_evals, (unsigned long long)c_lookups,
+                                   (unsigned long long)c_aps, (unsigned long long)c_relax};
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            for (int o = 16; o > 0; o >>= 1) c[j] += __shfl_down_sync(0xffffffffu, c[j], o);
+        if ((tid & 31) == 0) {
+#pragma unroll
+            for (int j = 0; j < 6; ++j) atomicAdd(&s_cnt[j], c[j]);
+        }
+    }
+    cluster.sync();                                   // every block's slots and counters final
+    // Block b writes the contiguous part [V b / C, V (b + 1) / C) of the row.
+    const int32_t lo = (int32_t)((int64_t)V * me / C), hi = (int32_t)((int64_t)V * (me + 1) / C);
+    for (int32_t i = lo + tid; i < hi; i += nthr) out[i] = *arr_of(i);
+    if (me == 0 && tid == 0) {
+        if (qa.status)
+            qa.status[q] = !valid ? EAT_ERR_INVALID : (total > 0 ? EAT_ERR_NO_CONVERGENCE : EAT_OK);
+        if (qa.counters) {
+            eat_counters r{};
+            r.rounds = rounds;
+            for (int b = 0; b < C; ++b) {
+                const unsigned long long *sc = cluster.map_shared_rank(s_cnt, b);
+                r.vertices += (int64_t)sc[0];
+                r.types += (int64_t)sc[1];
+                r.evals += (int64_t)sc[2];
+                r.lookups += (int64_t)sc[3];
+                r.aps += (int64_t)sc[4];
+                r.relaxed += (int64_t)sc[5];
+            }
+            qa.counters[q] = r;
+        }
+    }
+    cluster.sync();                                   // block 0 is done reading the others
+}
+
 template <int NETS>
 static const void *cta_kernel_ptr(int mem) {
     switch (mem) {
@@ -539,6 +756,27 @@ cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int 
                        int block, size_t smem, cudaStream_t st) {
     if (n_nets == 1) return launch_cta_t<1>(nets, n_nets, qa, mem, grid, block, smem, st);
     return launch_cta_t<EAT_MAX_NETS>(nets, n_nets, qa, mem, grid, block, smem, st);
+}
+
+const void *cluster_kernel() { return (const void *)eat_cluster_kernel<1>; }
+
+cudaError_t launch_cluster(const NetDev &net, const QueryArgs &qa, int cluster, int grid,
+                           int block, size_t smem, cudaStream_t st) {
+    NetTable<1> tab;
+    tab.net[0] = net;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, eat_cluster_kernel<1>, tab, qa);
 }
 
 cudaError_t launch_next_departure(const NetDev &N, const int32_t *types, const int32_t *times,

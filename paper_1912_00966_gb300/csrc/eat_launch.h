@@ -45,6 +45,11 @@ cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int 
 const void *async_kernel(int nets, int mem);
 cudaError_t launch_async(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
                          int block, size_t smem, cudaStream_t st);
+// Cluster mode: one cluster of `cluster` blocks per query on one network; grid =
+// n * cluster; arrivals and bitmaps spread over the cluster's shared memory.
+const void *cluster_kernel();
+cudaError_t launch_cluster(const NetDev &net, const QueryArgs &qa, int cluster, int grid,
+                           int block, size_t smem, cudaStream_t st);
 cudaError_t launch_next_departure(const NetDev &N, const int32_t *types, const int32_t *times,
                                   int32_t n, int32_t *out, cudaStream_t st);
 
