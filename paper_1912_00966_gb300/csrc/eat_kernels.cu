@@ -15,7 +15,9 @@
 //
 // CTA mode: one thread block owns one query at a time (persistent blocks take
 // queries from an atomic counter), so rounds are separated by one block barrier
-// and there is no grid-wide synchronisation and no spin-wait anywhere.
+// and there is no grid-wide synchronisation and no spin-wait.  The round-free
+// mode (eat_async_kernel) and the cluster mode (eat_cluster_kernel) are
+// described at their kernels below.
 //
 // Work items: when a stop v joins the next frontier, the thread that lowered e[v]
 // writes one (v, type) item per connection type leaving v into shared memory, so
