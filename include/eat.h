@@ -128,8 +128,8 @@ typedef struct {
     const int32_t *cl;
     const uint32_t *ap;
     /* The device layout, derived from the arrays above (Section IV-A's CL stride y):
-     *   cluster_entries[8 * n_types * y]  entry (t, k) for cluster k_min + k, one
-     *       32-byte record: {rel0 | rel1 << 16, sc0, sc1, next, x/2 | n << 24, v,
+     *   cluster_entries[8 * y * n_types]  entry (t, k) for cluster k_min + k at
+     *       record k * n_types + t (cluster-major), one 32-byte record: {rel0 | rel1 << 16, sc0, sc1, next, x/2 | n << 24, v,
      *       lambda | d << 24, row_ptr[v]}: the cluster's n APs, the first two inline
      *       with first terms base + rel, base = t0 + (k_min + k) * cluster_width, and
      *       sc = difference << 16 | terms, the others at ap_extra[x ..] (n = 255: the

@@ -541,9 +541,8 @@ int build_fused(HostNet &h) {
             const int32_t kl = (h.type_rec[4 * (size_t)t + 3] - t0) / W;
             const int32_t b = h.type_cl[t];
             int64_t x = xoff[t];
-            int32_t *row = &h.ce[(size_t)t * (size_t)Y * 8];
             for (int32_t kr = 0; kr < Y; ++kr) {
-                int32_t *e = row + (size_t)kr * 8;
+                int32_t *e = &h.ce[((size_t)kr * (size_t)T + (size_t)t) * 8];
                 const int32_t k = kmin + kr;
                 const int64_t cbase = (int64_t)t0 + (int64_t)k * W;
                 int32_t lo = 0, n = 0;
@@ -581,7 +580,7 @@ int build_fused(HostNet &h) {
             }
             int32_t next = EAT_INF;
             for (int32_t kr = (int32_t)Y - 1; kr >= 0; --kr) {
-                int32_t *e = row + (size_t)kr * 8;
+                int32_t *e = &h.ce[((size_t)kr * (size_t)T + (size_t)t) * 8];
                 e[3] = next;
                 if (((uint32_t)e[4] >> 24) > 0)
                     next = (int32_t)(t0 + (int64_t)(kmin + kr) * W + (e[0] & 0xffff));

@@ -121,7 +121,7 @@ __device__ __forceinline__ int32_t next_departure(const NetDev &N, int32_t t, in
                                                   int32_t &aps) {
     const int32_t k = cluster_slot(N, e);
     if (k >= N.y) return kInf;
-    const int4 *c = N.ce + 2 * ((int64_t)t * N.y + k);
+    const int4 *c = N.ce + 2 * ((int64_t)k * N.n_types + t);
     int4 a, b;
     load_entry(c, a, b);
     int32_t n, x;

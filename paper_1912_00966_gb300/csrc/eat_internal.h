@@ -17,8 +17,10 @@ namespace eat {
 // Device-side descriptor of one resident network (plain pointers into one blob).
 //
 // Device layout (derived from the logical arrays of HostNet by build_fused):
-//   ce[t*y + k]   32-byte entry of type t for cluster k_min + k, for every cluster
-//                 of the network (the paper's dense CL stride y), read in one load:
+//   ce[k*T + t]   32-byte entry of type t for cluster k_min + k, for every cluster
+//                 of the network (the paper's dense CL table, cluster-major so that
+//                 lookups at nearby times fall in one slab of T entries), read in
+//                 one load:
 //                   int4 {rel0 | rel1 << 16, sc0, sc1, next}
 //                   int4 {x/2 | n << 24, v, lambda | d << 24, row_ptr[v]}
 //                 the cluster's n APs: the first two inline with first terms
@@ -35,7 +37,7 @@ constexpr int32_t kMaxDuration = 1 << 24;
 
 struct NetDev {
     const int32_t *row_ptr;   // [V + 1] types by tail stop
-    const int4 *ce;           // [2 * T * y]
+    const int4 *ce;           // [2 * y * T], cluster-major
     const uint2 *apx;         // [n_apx]
     int32_t n_stops;
     int32_t n_types;

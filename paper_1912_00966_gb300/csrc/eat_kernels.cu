@@ -150,7 +150,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             auto relax = [&](int32_t e_u, int32_t k, int32_t t) {
                 ++c_types;
                 ++c_lookups;
-                const int4 *c = N.ce + 2 * ((int64_t)t * N.y + k);
+                const int4 *c = N.ce + 2 * ((int64_t)k * N.n_types + t);
                 int4 ca, cb;                                // cb = {x|n, v, lambda|d, row of v}
                 load_entry(c, ca, cb);
                 int32_t n, x;
@@ -406,7 +406,7 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
                 const int32_t eu = st_e[lo], kk = st_k[lo];
                 ++c_types;
                 ++c_lookups;
-                const int4 *c = N.ce + 2 * ((int64_t)t * N.y + kk);
+                const int4 *c = N.ce + 2 * ((int64_t)kk * N.n_types + t);
                 int4 ca, cb;                                 // cb = {x|n, v, lambda|d, row of v}
                 load_entry(c, ca, cb);
                 int32_t n, x;
@@ -578,7 +578,7 @@ eat_cluster_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs 
             ++c_types;
             ++c_lookups;
             int4 ca, cb;                                // cb = {x|n, v, lambda|d, row of v}
-            load_entry(N.ce + 2 * ((int64_t)t * N.y + k), ca, cb);
+            load_entry(N.ce + 2 * ((int64_t)k * N.n_types + t), ca, cb);
             int32_t n, x;
             entry_aps(cb, N.apx, n, x);
             const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, k), e_u, N.apx, c_aps);

@@ -119,7 +119,7 @@ __global__ void ladder_type_ap_kernel(LadderDev L, int32_t it) {
 __device__ __forceinline__ void cluster_ap_relax(const LadderDev &L, const NetDev &N, int32_t t,
                                                  int32_t eu, int32_t k, int32_t it) {
     int4 a, b;
-    load_entry(N.ce + 2 * ((int64_t)t * N.y + k), a, b);
+    load_entry(N.ce + 2 * ((int64_t)k * N.n_types + t), a, b);
     int32_t n, x, aps = 0;
     entry_aps(b, N.apx, n, x);
     const int32_t tc = cluster_lookup(a, n, x, cluster_base(N, k), eu, N.apx, aps);

@@ -297,7 +297,9 @@ def eat_net_host_view(net: Net) -> dict:
         "type_cl": arr(view.type_cl, T, np.int32),
         "cl": arr(view.cl, st["n_cl"], np.int32),
         "ap": arr(view.ap, 2 * st["n_ap"], np.uint32).reshape(-1, 2),
-        "cluster_entries": arr(view.cluster_entries, 8 * T * st["y"], np.int32).reshape(T, st["y"], 8),
+        # stored cluster-major; returned as [type, cluster, 8]
+        "cluster_entries": arr(view.cluster_entries, 8 * T * st["y"], np.int32)
+        .reshape(st["y"], T, 8).transpose(1, 0, 2).copy(),
         "ap_extra": arr(view.ap_extra, 2 * st["n_ap_extra"], np.uint32).reshape(-1, 2),
     }
 
