@@ -373,8 +373,9 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
  * sources/times (n queries, device memory) in nine rounds over all candidates:
  * the first warms up, the other eight are timed with CUDA events on `stream`,
  * each after a write of twice the L2 size so that every timing starts with the
- * network out of cache.  The earliest candidate whose median time is within 3 %
- * of the least median wins (closer differences are within timing noise), and
+ * network out of cache.  The earliest candidate whose median time is within 5 %
+ * of the least median wins (closer differences are within the spread between
+ * batches of one workload), and
  * is stored for batches of about n queries in the network; afterwards every
  * query call that leaves opts->block, opts->vwarp and opts->mode at 0 uses it
  * (a call with a round cap keeps the round-based mode).  The tuned shape is

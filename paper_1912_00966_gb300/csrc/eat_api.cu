@@ -974,9 +974,9 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
             }
         }
     }
-    // Least median time; shapes within 3 % of it count as tied (the spread of repeated
-    // timings of one shape), and a tie goes to the earliest candidate in the fixed
-    // order above, so that repeated tuning of one network settles on one shape.
+    // Least median time; shapes within 5 % of it count as tied (the spread of one
+    // shape's time over batches of the same workload), and a tie goes to the earliest
+    // candidate in the fixed order above, so that repeated tuning settles on one shape.
     float least = 1e30f;
     for (Cand &cd : cands) {
         if (cd.ms.size() != (size_t)kTimed) continue;
@@ -986,7 +986,7 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
     }
     int best_b = 512, best_v = 8, best_m = EAT_MODE_CTA;
     for (const Cand &cd : cands) {
-        if (cd.ms.size() == (size_t)kTimed && cd.ms[0] <= least * 1.03f) {
+        if (cd.ms.size() == (size_t)kTimed && cd.ms[0] <= least * 1.05f) {
             best_b = cd.b;
             best_v = cd.v;
             best_m = cd.m;
