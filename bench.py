@@ -481,7 +481,9 @@ LADDER_NAMES = {1: "Connection (Algorithm 4)", 2: "Connection-Type (Algorithm 5)
 def run_ladder(args):
     """Single-query latency of the paper's topology-driven variants (Table II's ladder, on
     the synthetic city network), with the flag read after every round and every
-    ceil(sqrt(d)) rounds (Section V-D), beside the frontier-driven kernel and the oracle."""
+    ceil(sqrt(d)) rounds (Section V-D), each with one launch per round and with the rounds
+    between flag reads replayed as a CUDA graph, beside the frontier-driven kernel and the
+    oracle."""
     import torch
     from paper_1912_00966_gb300 import eat
     world, rank, _ = dist_setup()
@@ -520,11 +522,13 @@ def run_ladder(args):
         clocks.mark()
         for v in range(1, 7):
             for every in (1, every_sqrt):
-                ms, st = timed(lambda s_, t_: eat.eat_ladder_query(lad, v, s_, t_, out=out,
-                                                                   flag_every=every)[1])
-                rows.append({"variant": LADDER_NAMES[v], "flag_every": every, "ms_per_query": ms,
-                             "rounds_mean": float(np.mean([x["rounds"] for x in st])),
-                             "flag_reads_mean": float(np.mean([x["flag_reads"] for x in st]))})
+                for graph in (False, True):
+                    ms, st = timed(lambda s_, t_: eat.eat_ladder_query(
+                        lad, v, s_, t_, out=out, flag_every=every, graph=graph)[1])
+                    rows.append({"variant": LADDER_NAMES[v], "flag_every": every,
+                                 "cuda_graph": graph, "ms_per_query": ms,
+                                 "rounds_mean": float(np.mean([x["rounds"] for x in st])),
+                                 "flag_reads_mean": float(np.mean([x["flag_reads"] for x in st]))})
         ms_front, _ = timed(lambda s_, t_: eat.eat_query(net, s_, t_, out))
         src_d = torch.as_tensor(qs.source).cuda()
         ts_d = torch.as_tensor(qs.t_s).cuda()

@@ -536,13 +536,16 @@ void eat_ladder_free(eat_ladder *l);
 /*
  * eat_ladder_query -- one query (s, t_s) with `variant` (enum eat_variant),
  * blocking.  arr_out: [n_stops] int32, host or device memory, as eat_query.
- * flag_every >= 1: rounds between flag reads.  stats may be NULL.  Calls on
- * one ladder are serialised internally.
+ * flag_every >= 1: rounds between flag reads.  graph != 0: the flag_every
+ * rounds between two reads are replayed as one CUDA graph (captured on first
+ * use per variant and cadence and kept with the ladder; the round index then
+ * lives on the device), else every round is its own launch.  stats may be
+ * NULL.  Calls on one ladder are serialised internally.
  * Errors: EAT_ERR_INVALID (bad variant, s out of range, flag_every < 1),
  * EAT_ERR_NO_CONVERGENCE (more than n_stops + flag_every rounds), EAT_ERR_CUDA.
  */
 int eat_ladder_query(eat_ladder *l, int32_t variant, int32_t s, int32_t t_s, int32_t flag_every,
-                     int32_t *arr_out, eat_ladder_stats *stats);
+                     int32_t graph, int32_t *arr_out, eat_ladder_stats *stats);
 
 /*
  * eat_ladder_host_view -- the variants' host copies, valid until

@@ -33,11 +33,19 @@ struct LadderDev {
     int32_t *e;                             // [V] arrivals
     int32_t *stamp;                         // [2 V] round stamps
     int32_t *last;                          // latest round that lowered an arrival
+    int32_t *round;                         // round index for launches that read it here
     int32_t V, T, E;
     int64_t C;
 };
 
 namespace {
+
+// Round index of a launch: the argument, or (when it is negative: graph replay, where
+// every launch of the graph is the same) the device counter that ladder_advance_kernel
+// moves on after each round.
+__device__ __forceinline__ int32_t round_of(const LadderDev &L, int32_t it) {
+    return it >= 0 ? it : __ldcg(L.round);
+}
 
 __device__ __forceinline__ bool ladder_active(const LadderDev &L, int32_t u, int32_t it) {
     return __ldcg(L.stamp + (int64_t)(it & 1) * L.V + u) == it;
@@ -60,11 +68,17 @@ __global__ void ladder_init_kernel(LadderDev L, int32_t s, int32_t t_s) {
         L.stamp[i] = i == s ? 0 : -1;
         L.stamp[L.V + i] = -1;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *L.last = -1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *L.last = -1;
+        *L.round = 0;
+    }
 }
 
+__global__ void ladder_advance_kernel(LadderDev L) { *L.round += 1; }
+
 // Algorithm 4: one thread per connection.
-__global__ void ladder_connection_kernel(LadderDev L, int32_t it) {
+__global__ void ladder_connection_kernel(LadderDev L, int32_t it_arg) {
+    const int32_t it = round_of(L, it_arg);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < L.C; c += stride) {
         const int32_t u = __ldg(L.cu + c);
@@ -76,7 +90,8 @@ __global__ void ladder_connection_kernel(LadderDev L, int32_t it) {
 }
 
 // Algorithm 5: one thread per type, getConnection by linear search.
-__global__ void ladder_type_kernel(LadderDev L, int32_t it) {
+__global__ void ladder_type_kernel(LadderDev L, int32_t it_arg) {
+    const int32_t it = round_of(L, it_arg);
     const int32_t stride = gridDim.x * blockDim.x;
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < L.T; t += stride) {
         const int4 r = __ldg(L.ty + t);
@@ -95,7 +110,8 @@ __global__ void ladder_type_kernel(LadderDev L, int32_t it) {
 
 // Section III-C: one thread per type, getConnectionFromAPs (Algorithm 6) over the
 // type's whole-day AP tuples.
-__global__ void ladder_type_ap_kernel(LadderDev L, int32_t it) {
+__global__ void ladder_type_ap_kernel(LadderDev L, int32_t it_arg) {
+    const int32_t it = round_of(L, it_arg);
     const int32_t stride = gridDim.x * blockDim.x;
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < L.T; t += stride) {
         const int4 r = __ldg(L.ty + t);
@@ -127,7 +143,8 @@ __device__ __forceinline__ void cluster_ap_relax(const LadderDev &L, const NetDe
 }
 
 // Section III-D: one thread per type, Cluster-AP lookup.
-__global__ void ladder_cluster_ap_kernel(LadderDev L, NetDev N, int32_t it) {
+__global__ void ladder_cluster_ap_kernel(LadderDev L, NetDev N, int32_t it_arg) {
+    const int32_t it = round_of(L, it_arg);
     const int32_t stride = gridDim.x * blockDim.x;
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < L.T; t += stride) {
         const int32_t u = __ldg(L.ty + t).x;
@@ -139,7 +156,8 @@ __global__ void ladder_cluster_ap_kernel(LadderDev L, NetDev N, int32_t it) {
 }
 
 // Section III-E: one thread per edge, all its types by Cluster-AP.
-__global__ void ladder_edge_kernel(LadderDev L, NetDev N, int32_t it) {
+__global__ void ladder_edge_kernel(LadderDev L, NetDev N, int32_t it_arg) {
+    const int32_t it = round_of(L, it_arg);
     const int32_t stride = gridDim.x * blockDim.x;
     for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < L.E; e += stride) {
         const int32_t u = __ldg(L.edge_u + e);
@@ -153,7 +171,8 @@ __global__ void ladder_edge_kernel(LadderDev L, NetDev N, int32_t it) {
 }
 
 // Section III-F: one warp per edge, the edge's types over the lanes.
-__global__ void ladder_warp_kernel(LadderDev L, NetDev N, int32_t it) {
+__global__ void ladder_warp_kernel(LadderDev L, NetDev N, int32_t it_arg) {
+    const int32_t it = round_of(L, it_arg);
     const int32_t lane = threadIdx.x & 31;
     const int32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (int32_t e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < L.E; e += nw) {
@@ -186,6 +205,11 @@ struct eat_ladder {
     cudaStream_t stream = nullptr;
     LadderDev dev{};
     int sms = 0;
+    struct Graph {
+        int variant, rounds;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;               // instantiated round groups, by (variant, rounds)
     std::mutex lock;
 };
 
@@ -242,7 +266,7 @@ int ladder_upload(eat_ladder *l) {
         {l->deps.data(), l->deps.size() * 4, 0}, {l->ap_ptr.data(), l->ap_ptr.size() * 4, 0},
         {apq.data(), (size_t)A * 16, 0}, {l->edge_ptr.data(), l->edge_ptr.size() * 4, 0},
         {l->edge_u.data(), (size_t)E * 4, 0},
-        {nullptr, (size_t)V * 4, 0}, {nullptr, (size_t)V * 8, 0}, {nullptr, 4, 0}};
+        {nullptr, (size_t)V * 4, 0}, {nullptr, (size_t)V * 8, 0}, {nullptr, 4, 0}, {nullptr, 4, 0}};
     size_t total = 0;
     for (Piece &q : p) {
         q.off = total;
@@ -275,6 +299,7 @@ int ladder_upload(eat_ladder *l) {
     L.e = (int32_t *)(b + p[11].off);
     L.stamp = (int32_t *)(b + p[12].off);
     L.last = (int32_t *)(b + p[13].off);
+    L.round = (int32_t *)(b + p[14].off);
     L.V = V;
     L.T = T;
     L.E = E;
@@ -287,6 +312,22 @@ int ladder_upload(eat_ladder *l) {
 }
 
 }  // namespace
+
+// One round of `variant`; it < 0: the kernels read the round from the device.
+static cudaError_t launch_round(eat_ladder *l, int32_t variant, int32_t it, int grid, int block,
+                                cudaStream_t st) {
+    const LadderDev &L = l->dev;
+    const NetDev &N = l->net->dev;
+    switch (variant) {
+        case EAT_VAR_CONNECTION: ladder_connection_kernel<<<grid, block, 0, st>>>(L, it); break;
+        case EAT_VAR_TYPE: ladder_type_kernel<<<grid, block, 0, st>>>(L, it); break;
+        case EAT_VAR_TYPE_AP: ladder_type_ap_kernel<<<grid, block, 0, st>>>(L, it); break;
+        case EAT_VAR_CLUSTER_AP: ladder_cluster_ap_kernel<<<grid, block, 0, st>>>(L, N, it); break;
+        case EAT_VAR_EDGE: ladder_edge_kernel<<<grid, block, 0, st>>>(L, N, it); break;
+        default: ladder_warp_kernel<<<grid, block, 0, st>>>(L, N, it); break;
+    }
+    return cudaGetLastError();
+}
 
 extern "C" {
 
@@ -364,6 +405,7 @@ void eat_ladder_free(eat_ladder *l) {
         int prev = -1;
         cudaGetDevice(&prev);
         cudaSetDevice(l->device);
+        for (const eat_ladder::Graph &g : l->graphs) cudaGraphExecDestroy(g.exec);
         if (l->stream) cudaStreamDestroy(l->stream);
         if (l->pinned) cudaFreeHost(l->pinned);
         if (l->blob) cudaFree(l->blob);
@@ -389,7 +431,7 @@ int eat_ladder_host_view(const eat_ladder *l, eat_ladder_view *view) {
 }
 
 int eat_ladder_query(eat_ladder *l, int32_t variant, int32_t s, int32_t t_s, int32_t flag_every,
-                     int32_t *arr_out, eat_ladder_stats *stats) {
+                     int32_t graph, int32_t *arr_out, eat_ladder_stats *stats) {
     clear_error();
     if (!l || !arr_out) return fail(EAT_ERR_INVALID, "NULL argument");
     if (l->device < 0) return fail(EAT_ERR_NO_DEVICE, "ladder was built host-only");
@@ -401,49 +443,68 @@ int eat_ladder_query(eat_ladder *l, int32_t variant, int32_t s, int32_t t_s, int
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(l->device);
-    const LadderDev &L = l->dev;
-    const NetDev &N = l->net->dev;
     cudaStream_t st = l->stream;
     const int block = 256, grid = l->sms * 8;
-    ladder_init_kernel<<<grid, block, 0, st>>>(L, s, t_s);
     const int32_t cap = l->n_stops + flag_every;
     int32_t it = 0, reads = 0;
     int rc = EAT_OK;
-    cudaError_t e = cudaGetLastError();
-    for (; e == cudaSuccess; ++it) {
-        switch (variant) {
-            case EAT_VAR_CONNECTION: ladder_connection_kernel<<<grid, block, 0, st>>>(L, it); break;
-            case EAT_VAR_TYPE: ladder_type_kernel<<<grid, block, 0, st>>>(L, it); break;
-            case EAT_VAR_TYPE_AP: ladder_type_ap_kernel<<<grid, block, 0, st>>>(L, it); break;
-            case EAT_VAR_CLUSTER_AP: ladder_cluster_ap_kernel<<<grid, block, 0, st>>>(L, N, it); break;
-            case EAT_VAR_EDGE: ladder_edge_kernel<<<grid, block, 0, st>>>(L, N, it); break;
-            default: ladder_warp_kernel<<<grid, block, 0, st>>>(L, N, it); break;
-        }
-        e = cudaGetLastError();
-        if (e != cudaSuccess || (it + 1) % flag_every) {
-            if (e == cudaSuccess && it >= cap) {
-                rc = fail(EAT_ERR_NO_CONVERGENCE, "round cap reached");
-                break;
+    cudaError_t e = cudaSuccess;
+    cudaGraphExec_t exec = nullptr;
+    if (graph) {
+        for (const eat_ladder::Graph &gr : l->graphs)
+            if (gr.variant == variant && gr.rounds == flag_every) exec = gr.exec;
+        if (!exec) {   // capture flag_every (round, advance) pairs once per (variant, cadence)
+            cudaGraph_t gph = nullptr;
+            e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            for (int32_t r = 0; r < flag_every && e == cudaSuccess; ++r) {
+                e = launch_round(l, variant, -1, grid, block, st);
+                if (e == cudaSuccess) {
+                    ladder_advance_kernel<<<1, 1, 0, st>>>(l->dev);
+                    e = cudaGetLastError();
+                }
             }
-            continue;
+            const cudaError_t e2 = cudaStreamEndCapture(st, &gph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, gph, 0);
+            if (gph) cudaGraphDestroy(gph);
+            if (e == cudaSuccess) l->graphs.push_back({variant, flag_every, exec});
         }
-        e = cudaMemcpyAsync(l->pinned, L.last, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        ++reads;
-        if (e == cudaSuccess && *l->pinned < it) {   // round `it` lowered nothing
+    }
+    if (e == cudaSuccess) {
+        ladder_init_kernel<<<grid, block, 0, st>>>(l->dev, s, t_s);
+        e = cudaGetLastError();
+    }
+    while (e == cudaSuccess) {
+        if (graph) {
+            e = cudaGraphLaunch(exec, st);
+            it += flag_every;
+        } else {
+            e = launch_round(l, variant, it, grid, block, st);
             ++it;
-            break;
+            if (e != cudaSuccess || it % flag_every) {
+                if (e == cudaSuccess && it > cap) rc = fail(EAT_ERR_NO_CONVERGENCE, "round cap reached");
+                if (rc) break;
+                continue;
+            }
         }
-        if (it >= cap) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(l->pinned, l->dev.last, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        ++reads;
+        if (*l->pinned < it - 1) break;          // the last round lowered nothing
+        if (it > cap) {
             rc = fail(EAT_ERR_NO_CONVERGENCE, "round cap reached");
             break;
         }
     }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(arr_out, L.e, (size_t)l->n_stops * 4, cudaMemcpyDefault, st);
+        e = cudaMemcpyAsync(arr_out, l->dev.e, (size_t)l->n_stops * 4, cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (prev >= 0) cudaSetDevice(prev);
-    if (e != cudaSuccess) return fail(EAT_ERR_CUDA, std::string("eat_ladder_query: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EAT_ERR_CUDA, std::string("eat_ladder_query: ") + cudaGetErrorString(e));
+    }
     if (stats) {
         stats->rounds = it;
         stats->flag_reads = reads;

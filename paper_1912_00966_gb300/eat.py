@@ -156,7 +156,8 @@ _sig("eat_ladder_build", ctypes.c_int, [ctypes.POINTER(eat_connections),
                                         ctypes.POINTER(eat_build_opts), ctypes.POINTER(_vp)])
 _sig("eat_ladder_free", None, [_vp])
 _sig("eat_ladder_query", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                        ctypes.c_int32, _vp, ctypes.POINTER(eat_ladder_stats)])
+                                        ctypes.c_int32, ctypes.c_int32, _vp,
+                                        ctypes.POINTER(eat_ladder_stats)])
 _sig("eat_ladder_host_view", ctypes.c_int, [_vp, ctypes.POINTER(eat_ladder_view)])
 
 EXPORTED = ("eat_autotune", "eat_server_create", "eat_server_submit", "eat_server_poll", "eat_server_get_stats",
@@ -474,7 +475,8 @@ def eat_ladder_build(n_stops, u, v, dep, dur, cluster_width=0, t0=0, device=0) -
     return Ladder(h.value)
 
 
-def eat_ladder_query(ladder: Ladder, variant, s, t_s, out=None, flag_every=1, n_stops=None):
+def eat_ladder_query(ladder: Ladder, variant, s, t_s, out=None, flag_every=1, graph=False,
+                     n_stops=None):
     """One blocking query with a topology-driven variant; returns (out, stats dict)."""
     if out is None:
         if n_stops is None:
@@ -482,7 +484,8 @@ def eat_ladder_query(ladder: Ladder, variant, s, t_s, out=None, flag_every=1, n_
         out = np.empty(int(n_stops), dtype=np.int32)
     st = eat_ladder_stats()
     _check(_lib.eat_ladder_query(ladder.handle, int(variant), int(s), int(t_s), int(flag_every),
-                                 _ptr(out), ctypes.byref(st)), "eat_ladder_query")
+                                 int(bool(graph)), _ptr(out), ctypes.byref(st)),
+           "eat_ladder_query")
     return out, {"rounds": st.rounds, "flag_reads": st.flag_reads}
 
 

@@ -45,10 +45,10 @@ def test_small_grid_all_variants(eat, small, variant):
     tss = [28800] + q.t_s.tolist()
     for s, t_s in zip(srcs, tss):
         want = oracle.csa(sc, s, t_s)
-        for every in (1, 3):
-            got, st = eat.eat_ladder_query(lad, variant, s, t_s, flag_every=every,
+        for every, graph in ((1, False), (3, False), (1, True), (4, True)):
+            got, st = eat.eat_ladder_query(lad, variant, s, t_s, flag_every=every, graph=graph,
                                            n_stops=tt.n_stops)
-            assert np.array_equal(got, want), (variant, s, t_s, every)
+            assert np.array_equal(got, want), (variant, s, t_s, every, graph)
             assert st["rounds"] % every == 0 and st["flag_reads"] == st["rounds"] // every
             assert 1 <= st["rounds"] <= tt.n_stops + every
 
@@ -76,10 +76,12 @@ def test_city_variants(eat, city, variant):
     out = torch.full((tt.n_stops,), -7, dtype=torch.int32, device="cuda")
     for i in range(3):
         want = oracle.csa(sc, int(q.source[i]), int(q.t_s[i]))
-        _, st = eat.eat_ladder_query(lad, variant, int(q.source[i]), int(q.t_s[i]), out=out,
-                                     flag_every=8)
-        assert np.array_equal(out.cpu().numpy(), want), (variant, i)
-        assert st["rounds"] % 8 == 0
+        for graph in (False, True):
+            out.fill_(-7)
+            _, st = eat.eat_ladder_query(lad, variant, int(q.source[i]), int(q.t_s[i]), out=out,
+                                         flag_every=8, graph=graph)
+            assert np.array_equal(out.cpu().numpy(), want), (variant, i, graph)
+            assert st["rounds"] % 8 == 0
 
 
 def test_invalid_arguments(eat, small):

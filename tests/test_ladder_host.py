@@ -63,7 +63,7 @@ def test_query_needs_a_device(eat):
     tt = synth.small_grid()
     lad = eat.eat_ladder_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=-1)
     with pytest.raises(eat.EatError) as ei:
-        eat.eat_ladder_query(lad, eat.EAT_VAR_TYPE, 0, 28800, n_stops=tt.n_stops)
+        eat.eat_ladder_query(lad, eat.EAT_VAR_TYPE, 0, 28800, graph=True, n_stops=tt.n_stops)
     assert ei.value.code == eat.EAT_ERR_NO_DEVICE
     with pytest.raises(eat.EatError) as ei:
         eat.eat_ladder_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=-1,
