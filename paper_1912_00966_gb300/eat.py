@@ -373,7 +373,7 @@ def eat_query_batch_noalloc(net: Net, sources, times, out, stream=None, **opts):
 
 def eat_autotune(net: Net, sources, times, stream=None) -> dict:
     """Time the candidate launch shapes on a sample batch (device int32 arrays) and keep the
-    fastest for this network and batch size; returns {"block": b, "vwarp": v}."""
+    fastest for this network and batch size; returns {"block": b, "vwarp": v, "mode": m}."""
     o = eat_query_opts()
     _check(_lib.eat_autotune(net.handle, _ptr(sources), _ptr(times), int(sources.shape[0]),
                              ctypes.byref(o), _stream_handle(stream)), "eat_autotune")
