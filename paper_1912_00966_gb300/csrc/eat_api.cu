@@ -314,9 +314,19 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     else if (place == EAT_PLACE_GLOBAL_ARR || (place == EAT_PLACE_AUTO && fits(1))) p.mem = 1;
     else p.mem = 2;
 
-    // Largest queue capacity that keeps the most blocks per SM the threads allow.
+    // Largest queue capacity that keeps the most blocks per SM the threads and the
+    // registers allow (shared memory is the only other limit, and the one sized here).
     const size_t b0 = p.mem == 3 ? base(1) + (size_t)p.smem_arr_cap * 4 : base(p.mem);
-    const int max_blocks = std::max(1, 2048 / p.block);
+    int reg_blocks = 0;
+    {
+        DeviceGuard guard(dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&reg_blocks, cta_kernel(p.nets, p.mem),
+                                                          p.block, 0) != cudaSuccess) {
+            cudaGetLastError();
+            reg_blocks = 0;
+        }
+    }
+    const int max_blocks = std::max(1, std::min(2048 / p.block, reg_blocks > 0 ? reg_blocks : 2048));
     p.qcap = (int32_t)qmin;
     for (int b = max_blocks; b >= 1; --b) {
         const size_t budget = std::min(limit, d.smem_per_sm / (size_t)b - d.reserve);
