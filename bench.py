@@ -55,7 +55,7 @@ BYTES = {"vertices": 20, "types": 16, "evals": 4, "lookups": 8, "aps": 16, "rela
 # the per-query traffic of the 1,024-query step too); keyed by the kernel source hash
 # so that a changed kernel reports null until it is profiled again.
 NCU_TRAFFIC_PER_QUERY = {"city": ("f57331be6d14ed08", 63322112 / 256),
-                         "large": ("f57331be6d14ed08", 2682068896 / 152)}
+                         "large": ("f57331be6d14ed08", 2698173752 / 152)}
 
 
 def kernel_hash() -> str:
