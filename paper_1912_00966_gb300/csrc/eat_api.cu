@@ -251,9 +251,10 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     if (tuned && n > 0) {
         int cls = 0;
         while (cls < 31 && (1 << (cls + 1)) <= n) ++cls;
-        tb = tuned->tuned_block[cls];
-        tv = tuned->tuned_vwarp[cls];
-        tm = tuned->tuned_mode[cls];
+        const uint32_t sh = tuned->tuned[cls].load(std::memory_order_relaxed);
+        tb = (int)(sh & 0xffffu);
+        tv = (int)((sh >> 16) & 0xffu);
+        tm = (int)(sh >> 24);
     }
     // Default shape: with at most one query per SM each query gets a 1,024-thread
     // block (measured faster for single queries and small batches); fuller batches
@@ -1011,9 +1012,8 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
     if (rc) return rc;
     int cls = 0;
     while (cls < 31 && (1 << (cls + 1)) <= n) ++cls;
-    net->tuned_block[cls] = best_b;
-    net->tuned_vwarp[cls] = best_v;
-    net->tuned_mode[cls] = best_m;
+    net->tuned[cls].store((uint32_t)best_b | (uint32_t)best_v << 16 | (uint32_t)best_m << 24,
+                          std::memory_order_relaxed);
     if (best) {
         *best = eat_query_opts{};
         best->block = best_b;

@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -85,10 +86,10 @@ struct eat_net {
     mutable size_t ws_bytes = 0;
     mutable void *stage = nullptr;
     mutable size_t stage_bytes = 0;
-    // Launch shapes chosen by eat_autotune, per batch-size class (log2 of n).
-    mutable int32_t tuned_block[32] = {0};
-    mutable int32_t tuned_vwarp[32] = {0};
-    mutable int32_t tuned_mode[32] = {0};
+    // Launch shape chosen by eat_autotune per batch-size class (log2 of n), packed as
+    // block | vwarp << 16 | mode << 24 (0 = none) so that a query call on another
+    // thread reads one whole shape.
+    mutable std::atomic<uint32_t> tuned[32] = {};
 };
 
 namespace eat {
