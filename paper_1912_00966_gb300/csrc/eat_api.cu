@@ -93,7 +93,8 @@ static int device_info(int dev, DeviceInfo &out) {
         DeviceGuard guard(dev);
         for (int nets : {1, EAT_MAX_NETS})
             for (int mem = 0; mem < 4; ++mem)
-                for (const void *k : {cta_kernel(nets, mem), async_kernel(nets, mem), cluster_kernel()}) {
+                for (const void *k : {cta_kernel(nets, mem), async_kernel(nets, mem), cluster_kernel(),
+                                      cta_kernel(1, 0, true)}) {
                     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(d.smem_optin - d.reserve));
                     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -124,6 +125,7 @@ struct Plan {
     int nets = 1;
     bool async = false;           // round-free kernel (EAT_MODE_ASYNC)
     int cluster = 0;              // blocks per query in cluster mode (EAT_MODE_CLUSTER), else 0
+    bool pack = false;            // one int32 per queued item (small networks, shared arrivals)
 };
 
 static constexpr size_t kWsHeader = 256;   // work counter + internal status / counters
@@ -315,13 +317,17 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     else if (place == EAT_PLACE_GLOBAL_ARR || (place == EAT_PLACE_AUTO && fits(1))) p.mem = 1;
     else p.mem = 2;
 
+    // Items take one int32 instead of two on one network small enough for the packed
+    // form (twice the queue in the same shared memory).
+    p.pack = p.mem == 0 && n_nets == 1 && tuned && vmax <= 32767 && tuned->host.n_types <= 65535;
+    const size_t qbytes = p.pack ? kQueueEntryBytes / 2 : kQueueEntryBytes;
     // Largest queue capacity that keeps the most blocks per SM the threads and the
     // registers allow (shared memory is the only other limit, and the one sized here).
     const size_t b0 = p.mem == 3 ? base(1) + (size_t)p.smem_arr_cap * 4 : base(p.mem);
     int reg_blocks = 0;
     {
         DeviceGuard guard(dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&reg_blocks, cta_kernel(p.nets, p.mem),
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&reg_blocks, cta_kernel(p.nets, p.mem, p.pack),
                                                           p.block, 0) != cudaSuccess) {
             cudaGetLastError();
             reg_blocks = 0;
@@ -331,8 +337,8 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     p.qcap = (int32_t)qmin;
     for (int b = max_blocks; b >= 1; --b) {
         const size_t budget = std::min(limit, d.smem_per_sm / (size_t)b - d.reserve);
-        if (d.smem_per_sm / (size_t)b < d.reserve || b0 + kQueueEntryBytes * qmin > budget) continue;
-        size_t cap = (budget - b0) / kQueueEntryBytes;
+        if (d.smem_per_sm / (size_t)b < d.reserve || b0 + qbytes * qmin > budget) continue;
+        size_t cap = (budget - b0) / qbytes;
         cap = std::min(cap, (size_t)std::max(vmax, 1));
         if (cap >= 64) cap &= ~(size_t)31;
         p.qcap = (int32_t)std::max(cap, qmin);
@@ -340,13 +346,13 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     }
     p.smem_mask_off = p.mem == 0 ? (int32_t)(arr_bytes / 4) : p.mem == 3 ? p.smem_arr_cap : 0;
     p.smem_q_off = p.smem_mask_off + (p.mem != 2 ? 2 * p.mask_words : 0);
-    p.smem = b0 + kQueueEntryBytes * (size_t)p.qcap;
+    p.smem = b0 + qbytes * (size_t)p.qcap;
 
     int per_sm = 0;
     cudaError_t e;
     {
         DeviceGuard guard(dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cta_kernel(p.nets, p.mem),
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cta_kernel(p.nets, p.mem, p.pack),
                                                           p.block, p.smem);
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
@@ -449,7 +455,7 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
     for (int i = 0; i < n_nets; ++i) devs[i] = nets[i]->dev;
     e = p.cluster ? launch_cluster(devs[0], qa, p.cluster, p.grid, p.block, p.smem, st)
         : p.async ? launch_async(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st)
-                  : launch_cta(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st);
+                  : launch_cta(devs, n_nets, qa, p.mem, p.grid, p.block, p.smem, st, p.pack);
     if (e != cudaSuccess) return cuda_fail(e, "query kernel launch");
     return EAT_OK;
 }
@@ -1089,7 +1095,7 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     cudaError_t e = cudaMemsetAsync(qa.work, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-allocation scratch)");
     e = p.async ? launch_async(&net->dev, 1, qa, p.mem, grid, p.block, p.smem, st)
-                : launch_cta(&net->dev, 1, qa, p.mem, grid, p.block, p.smem, st);
+                : launch_cta(&net->dev, 1, qa, p.mem, grid, p.block, p.smem, st, p.pack);
     if (e != cudaSuccess) return cuda_fail(e, "query kernel launch");
     return EAT_OK;
 }

@@ -56,7 +56,11 @@ __device__ __forceinline__ int32_t load_arr(const int32_t *arr, int32_t i, bool 
 constexpr int32_t kNullItem = -1;           // hole left by a stop that spilled
 constexpr int32_t kFirstItem = INT32_MIN;    // flag on the first item of a stop
 
-template <int NETS, int ARR, bool SMEM_MASK>
+// Items are (stop, type) pairs in two int32 arrays per buffer, or, with PACK (networks
+// of at most 32,767 stops and 65,535 types), one word per item: first-item flag << 31 |
+// stop << 16 | type, which doubles the items a buffer holds in the same shared memory
+// (kNullItem is then no valid item: it would be stop 32,767, type 65,535).
+template <int NETS, int ARR, bool SMEM_MASK, bool PACK = false>
 __global__ void __launch_bounds__(1024, 1)
 eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) {
     extern __shared__ __align__(16) int32_t smem[];
@@ -130,9 +134,9 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
         int32_t c_vert = 0, c_types = 0, c_evals = 0, c_lookups = 0, c_aps = 0, c_relax = 0;
         while (n_items + n_spill > 0 && rounds < qa.max_rounds) {
             const int wr = rounds & 1, rd = wr ^ 1;
-            int32_t *const iu_rd = item_base + (2 * rd) * icap;
-            int32_t *const it_rd = iu_rd + icap;
-            int32_t *const iu_wr = item_base + (2 * wr) * icap;
+            int32_t *const iu_rd = item_base + (PACK ? rd : 2 * rd) * icap;
+            int32_t *const it_rd = iu_rd + icap;           // (unused with PACK)
+            int32_t *const iu_wr = item_base + (PACK ? wr : 2 * wr) * icap;
             int32_t *const it_wr = iu_wr + icap;
             const int32_t *const sp_rd = spill_base + (int64_t)rd * qa.vmax;
             int32_t *const sp_wr = spill_base + (int64_t)wr * qa.vmax;
@@ -172,11 +176,17 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                 if (atomicOr(pmask + (v >> 5), bit) & bit) return;   // already queued
                 const int32_t base = atomicAdd(&s_items[cs], d);
                 if (base + d <= icap) {
-                    iu_wr[base] = v | kFirstItem;
-                    it_wr[base] = ty.z;
-                    for (int32_t j = 1; j < d; ++j) {
-                        iu_wr[base + j] = v;
-                        it_wr[base + j] = ty.z + j;
+                    if (PACK) {
+                        const int32_t hv = (v << 16) | ty.z;
+                        iu_wr[base] = hv | kFirstItem;
+                        for (int32_t j = 1; j < d; ++j) iu_wr[base + j] = hv + j;
+                    } else {
+                        iu_wr[base] = v | kFirstItem;
+                        it_wr[base] = ty.z;
+                        for (int32_t j = 1; j < d; ++j) {
+                            iu_wr[base + j] = v;
+                            it_wr[base + j] = ty.z + j;
+                        }
                     }
                 } else {
                     for (int32_t j = base; j < icap; ++j) iu_wr[j] = kNullItem;
@@ -188,7 +198,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             for (int32_t i = tid; i < n_items; i += nthr) {
                 const int32_t raw = iu_rd[i];
                 if (raw == kNullItem) continue;
-                const int32_t u = raw & 0x7fffffff;
+                const int32_t u = PACK ? (raw >> 16) & 0x7fff : raw & 0x7fffffff;
                 if (raw < 0) {                              // first item of u
                     atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
                     ++c_vert;
@@ -199,7 +209,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                     ++c_types;
                     continue;
                 }
-                relax(e_u, k, it_rd[i]);
+                relax(e_u, k, PACK ? raw & 0xffff : it_rd[i]);
             }
             // Spilled stops: `vw` lanes per stop stride over its types.
             for (int32_t i = sub; i < n_spill; i += nsub) {
@@ -288,7 +298,6 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
     const int nthr = blockDim.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    const int nwarps = nthr >> 5;
     uint32_t *const mask = (uint32_t *)(smem + qa.smem_mask_off);
     // Per-warp staging of claimed stops: row begin, exclusive item prefix, e[u], cluster.
     int32_t *const stage = smem + qa.smem_q_off + warp * (4 * 32);
@@ -702,7 +711,8 @@ static const void *cta_kernel_ptr(int mem) {
     }
 }
 
-const void *cta_kernel(int nets, int mem) {
+const void *cta_kernel(int nets, int mem, bool pack) {
+    if (pack) return (const void *)eat_cta_kernel<1, kArrShared, true, true>;
     return nets == 1 ? cta_kernel_ptr<1>(mem) : cta_kernel_ptr<EAT_MAX_NETS>(mem);
 }
 
@@ -755,7 +765,13 @@ static cudaError_t launch_cta_t(const NetDev *nets, int n_nets, const QueryArgs 
 }
 
 cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
-                       int block, size_t smem, cudaStream_t st) {
+                       int block, size_t smem, cudaStream_t st, bool pack) {
+    if (pack) {
+        NetTable<1> tab;
+        tab.net[0] = nets[0];
+        eat_cta_kernel<1, kArrShared, true, true><<<grid, block, smem, st>>>(tab, qa);
+        return cudaGetLastError();
+    }
     if (n_nets == 1) return launch_cta_t<1>(nets, n_nets, qa, mem, grid, block, smem, st);
     return launch_cta_t<EAT_MAX_NETS>(nets, n_nets, qa, mem, grid, block, smem, st);
 }

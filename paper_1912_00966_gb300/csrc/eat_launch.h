@@ -38,9 +38,11 @@ struct QueryArgs {
 // mem: 0 = arrivals and bitmaps in shared memory, 1 = arrivals global / bitmaps
 // shared, 2 = both global, 3 = bitmaps shared and arrivals shared per query when
 // the query's network fits.  nets: 1 or EAT_MAX_NETS (kernel table size).
-const void *cta_kernel(int nets, int mem);
+// pack: one int32 per item (one network of at most 32,767 stops and 65,535 types,
+// arrivals and bitmaps in shared memory).
+const void *cta_kernel(int nets, int mem, bool pack = false);
 cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
-                       int block, size_t smem, cudaStream_t st);
+                       int block, size_t smem, cudaStream_t st, bool pack = false);
 // Asynchronous (round-free) kernel; mem 0, 1 or 3 as above (bitmap always shared).
 const void *async_kernel(int nets, int mem);
 cudaError_t launch_async(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
