@@ -54,8 +54,8 @@ BYTES = {"vertices": 20, "types": 16, "evals": 4, "lookups": 8, "aps": 16, "rela
 # (city: one 256-query launch; large: one 152-query launch, one query per SM, taken as
 # the per-query traffic of the 1,024-query step too); keyed by the kernel source hash
 # so that a changed kernel reports null until it is profiled again.
-NCU_TRAFFIC_PER_QUERY = {"city": ("f57331be6d14ed08", 63322112 / 256),
-                         "large": ("f57331be6d14ed08", 2698173752 / 152)}
+NCU_TRAFFIC_PER_QUERY = {"city": ("f3214bc03fae8b69", 63372800 / 256),
+                         "large": ("f3214bc03fae8b69", 2708783048 / 152)}
 
 
 def kernel_hash() -> str:
