@@ -9,13 +9,14 @@ one batch of 256 queries (random source with departures, t_s uniform in
 Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on the
 launching stream; L2 is flushed (a 256 MB buffer is written) before every step,
 outside the events; inputs are resident in device memory before timing starts.
-`e2e` repeats the measurement through the C ABI with pinned host buffers, so each
-step includes the host->device copy of the queries and the device->host copy of
-every arrival row.
+`e2e` repeats the measurement through the C ABI with page-locked host buffers, so
+each step includes moving the queries to the GPU and every arrival row back to host
+memory (the kernel reads the queries and writes each converged row to host memory
+in place).
 
 Roofline: algorithmic bytes per launch come from the kernel's own per-query work
-counters (stops expanded, types examined, AP records read, relaxations) times
-fixed per-unit byte figures; see the design doc for the figures.
+counters (stops expanded, types examined, AP records read, relaxations) times the
+fixed per-unit byte figures in BYTES below.
 
 `--impl reference` times the CPU oracle (connection scan, Algorithm 1) on the host
 cores on the same queries instead.
@@ -43,7 +44,7 @@ BATCH = 256
 FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
 
-# Per-unit algorithmic bytes (the survey's figures): per expanded stop 8 B frontier
+# Per-unit algorithmic bytes of the method's data structures: per expanded stop 8 B frontier
 # entry + 4 B e[u] + 8 B row offsets; per examined type 16 B type record; per type
 # that reads e[v] 4 B; per cluster lookup 8 B of cluster offsets; per AP record 16 B;
 # per successful relaxation 4 B atomic write + 8 B frontier push; per query 4 B x V
