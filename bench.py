@@ -51,12 +51,15 @@ FALLBACK_HBM_GBS = 6800.0
 # initialisation + 4 B x V result row.
 BYTES = {"vertices": 20, "types": 16, "evals": 4, "lookups": 8, "aps": 16, "relaxed": 12}
 
-# DRAM bytes per query of the CTA kernel, from the ncu captures summarised in profiles/
-# (city: one 256-query launch; large: one 152-query launch, one query per SM, taken as
+# DRAM bytes per query of the timed kernel, from the ncu captures summarised in profiles/
+# (city: one 256-query launch of the paired kernel; large: one 152-query launch of the
+# per-query kernel, one query per SM, taken as
 # the per-query traffic of the 1,024-query step too); keyed by the kernel source hash
-# so that a changed kernel reports null until it is profiled again.
-NCU_TRAFFIC_PER_QUERY = {"city": ("f3214bc03fae8b69", 63372800 / 256),
-                         "large": ("f3214bc03fae8b69", 2708783048 / 152)}
+# and the kernel's name, so that a changed kernel reports null until it is profiled again.
+NCU_TRAFFIC_PER_QUERY = {"city": ("55e3460f743d8757", "eat_pair_kernel", 63022080 / 256),
+                         "large": ("55e3460f743d8757", "eat_cta_kernel", 2701359592 / 152)}
+KERNEL_OF_MODE = {1: "eat_cta_kernel", 2: "eat_cluster_kernel", 3: "eat_async_kernel",
+                  4: "eat_pair_kernel"}
 
 
 def kernel_hash() -> str:
@@ -633,18 +636,28 @@ def run_ours(args):
         sample = synth.random_queries(tt, batch, 0xB0 - 1)
         tuned = eat.eat_autotune(net, torch.as_tensor(sample.source).cuda(),
                                  torch.as_tensor(sample.t_s).cuda())
+    shape = eat.eat_launch_shape(net, batch, **opts)      # the shape the timed launches run
     ws = torch.empty(eat.eat_workspace_bytes(net, batch, **opts), dtype=torch.uint8, device="cuda")
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(n_steps)]
 
+    # Work counters of every step's batch come from an untimed pass over the same
+    # queries: the timed launches run without counters (the paired kernel has a
+    # separate counting build), and a query's counts vary only slightly between runs
+    # (the order of relaxations within a round is not fixed).
+    for i in range(n_steps):
+        eat.eat_query_batch(net, src_d[i], ts_d[i], out, workspace=ws, stream=stream,
+                            counters=cnt[i], **opts)
+    torch.cuda.synchronize()
+
     def step(i):
         flush.fill_(i)
         a, b = evs[i]
         a.record(stream)
         eat.eat_query_batch(net, src_d[i], ts_d[i], out, workspace=ws, stream=stream,
-                            status=status[i], counters=cnt[i], **opts)
+                            status=status[i], **opts)
         b.record(stream)
 
     with ClockSampler(dev) as clocks:
@@ -727,13 +740,11 @@ def run_ours(args):
 
     peak, peak_kind = measured_peak()
     achieved = per_launch / (mean_ms / 1e3) / 1e9
-    mode_used = (tuned or {}).get("mode", args.mode)
-    kernel_name = "eat_async_kernel" if mode_used == eat.EAT_MODE_ASYNC else "eat_cta_kernel"
+    kernel_name = KERNEL_OF_MODE[shape["mode"]]
     h = kernel_hash()
     traffic = None
-    if (kernel_name == "eat_cta_kernel" and args.workload in NCU_TRAFFIC_PER_QUERY
-            and NCU_TRAFFIC_PER_QUERY[args.workload][0] == h):
-        traffic = NCU_TRAFFIC_PER_QUERY[args.workload][1] * batch
+    if args.workload in NCU_TRAFFIC_PER_QUERY and NCU_TRAFFIC_PER_QUERY[args.workload][:2] == (h, kernel_name):
+        traffic = NCU_TRAFFIC_PER_QUERY[args.workload][2] * batch
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -785,8 +796,8 @@ def run_ours(args):
         "csa_equivalent_connections_per_s": csa_conn / (gpu_s / world),
         "subtrips": {0: "none", 1: "sqrt(k) per trip", 2: "sqrt(mean trip length)"}[args.subtrips],
         "cluster_width_s": args.cluster_width,
-        "launch_shape": tuned if tuned else {"block": args.block, "vwarp": args.vwarp,
-                                             "mode": args.mode},
+        "launch_shape": {**{k: shape[k] for k in ("block", "vwarp", "mode")},
+                         "chosen_by": "autotuner" if tuned else "library default or flags"},
         "without_subtrips": None if base_ms is None else
             {"value": batch / (base_ms / 1e3), "unit": "queries/s", "ms_per_step": base_ms},
         "build_s": t_build,

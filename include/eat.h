@@ -161,7 +161,8 @@ typedef struct {
     int32_t max_rounds;      /* round cap; 0 = n_stops + 1 (always enough: every
                                 productive round fixes at least one more stop) */
     int32_t block;           /* threads per CTA: 0 = automatic (the tuned shape, else 1024
-                                when the batch has at most one query per SM, else 512);
+                                when the batch has at most one query per SM or runs in
+                                the paired mode, else 512);
                                 else 64..1024, multiple of 32 */
     int32_t vwarp;           /* lanes per active stop (1, 2, 4, 8, 16 or 32); 0 = automatic */
     int32_t mode;            /* EAT_MODE_* */
@@ -195,7 +196,15 @@ enum eat_mode {
     EAT_MODE_ASYNC = 3  /* one thread block per query, no rounds: warps claim pending stops
                            from a bitmap and relax their types as soon as they appear;
                            needs the bitmap (n_stops bits) in shared memory; the round cap
-                           does not apply and counters.rounds is 0 */
+                           does not apply and counters.rounds is 0 */,
+    EAT_MODE_PAIR = 4   /* two queries per 1,024-thread block sharing its rounds, on one
+                           network of at most 32,767 stops and 65,535 connection types
+                           whose two arrival rows fit in one block's shared memory: when
+                           one query converges its threads go to the other and the slot
+                           takes the next query.  EAT_MODE_AUTO picks it (unless a tuned
+                           shape or opts->block says otherwise) for batches of more
+                           queries than SMs on one network of 8,192 stops or more; never
+                           automatically in eat_query_batch_noalloc */
 };
 
 /* Error message of the calling thread's last failed call ("" if none). */
@@ -303,6 +312,16 @@ size_t eat_workspace_bytes(const eat_net *const *nets, int32_t n_nets, int32_t n
                            const eat_query_opts *opts);
 
 /*
+ * eat_launch_shape -- the launch shape eat_query_batch(_multi) would use for n
+ * queries over the given networks with these options (opts may be NULL): *shape
+ * receives a copy of *opts with block, vwarp, mode (EAT_MODE_CTA, _CLUSTER,
+ * _ASYNC or _PAIR, never _AUTO) and cluster filled in.  Nothing is launched.
+ * Returns EAT_OK, or the error the batch call would report for these options.
+ */
+int eat_launch_shape(const eat_net *const *nets, int32_t n_nets, int32_t n,
+                     const eat_query_opts *opts, eat_query_opts *shape);
+
+/*
  * eat_query_batch -- n independent queries (sources[i], times[i]) on one
  * network, in one launch (batching across queries is this library's addition;
  * each query follows the same algorithm as eat_query).
@@ -369,7 +388,9 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
  * sweeps the virtual-warp size by hand, Section V-B).  Candidates, in this
  * order: block sizes 512, 1024 and 256 threads, each with the round-based mode
  * and vwarp 8, 4, 16, 2, 32 lanes per spilled stop, then with the asynchronous
- * mode, as far as they fit the device.  They are run on the sample batch
+ * mode, as far as they fit the device; when n exceeds the SM count, also the
+ * paired mode with vwarp 8, 4 and 16 (placed first on networks of 8,192 stops or
+ * more, where it is the default, else last).  They are run on the sample batch
  * sources/times (n queries, device memory) in nine rounds over all candidates:
  * the first warms up, the other eight are timed with CUDA events on `stream`,
  * each after a write of twice the L2 size so that every timing starts with the

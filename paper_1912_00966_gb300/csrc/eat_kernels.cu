@@ -90,7 +90,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
         const int q = s_q;
         if (q >= qa.n) break;
 
-        const int ni = (NETS == 1 || qa.net_idx == nullptr) ? 0 : __ldg(qa.net_idx + q);
+        const int ni = qa.net_idx == nullptr ? 0 : __ldg(qa.net_idx + q);
         const bool net_ok = (unsigned)ni < (unsigned)qa.n_nets;
         const NetDev &N = nets.net[net_ok ? ni : 0];
         const int32_t V = N.n_stops;
@@ -270,6 +270,275 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
     }
 }
 
+// ------------------------------------------------------------------ paired mode
+//
+// Two queries on one small network share a 1,024-thread block and its rounds: both
+// arrival rows and their bitmaps sit in shared memory, and every round hands the
+// items of both queries to all threads.  When one query converges its threads go
+// to the other (and the slot takes the next query), so a block is not left with
+// half its threads idle behind its deeper query; batches larger than the SM count
+// fill every SM with one block.  Items are packed as in eat_cta_kernel.  Slot 0's
+// items fill a buffer from the front, slot 1's from the back; one 32-bit counter
+// per round reserves both (slot 0 in the low half, slot 1 in the high half: a slot
+// reserves at most one item per connection type in a round, and there are at most
+// 65,535 types), so a reservation fits if the two totals before it plus its own
+// items stay within the buffer.  Once one does not, none after it does: the
+// counter state before that first failure (saved by the failing thread) gives each
+// slot's valid items.
+constexpr int kSlots = 2;
+
+// Per-thread work counters of both slots (COUNT builds only): vertices, types,
+// evaluations, lookups, AP records, relaxations.
+struct PairCounters {
+    int32_t c[kSlots][6];
+    __device__ __forceinline__ void add(int j, int k, int32_t x) {
+        if (j) c[1][k] += x;
+        else c[0][k] += x;
+    }
+};
+
+template <bool COUNT>
+__global__ void __launch_bounds__(1024, 1)
+eat_pair_kernel(const __grid_constant__ NetTable<1> nets, const QueryArgs qa) {
+    extern __shared__ __align__(16) int32_t smem[];
+    __shared__ uint32_t s_res[3];               // items reserved per round (rotating)
+    __shared__ uint32_t s_cross[3];             // reservations before the first that failed
+    __shared__ int32_t s_spill[3][kSlots];      // stops spilled per round and slot
+    __shared__ int32_t s_q[kSlots];
+    __shared__ unsigned long long s_cnt[kSlots][6];
+
+    const NetDev &N = nets.net[0];
+    const int32_t V = N.n_stops;
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    const int vw = 1 << qa.vw_log2;
+    const int lane = tid & (vw - 1);
+    const int sub = tid >> qa.vw_log2;
+    const int nsub = nthr >> qa.vw_log2;
+    const int32_t icap = qa.qcap;               // items per buffer, both slots together
+    const int32_t vpad = qa.smem_arr_cap;       // ints per arrival row
+    const int32_t nwords = (V + 31) >> 5;
+    PairCounters pc;
+#pragma unroll
+    for (int j = 0; j < kSlots; ++j)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pc.c[j][k] = 0;
+    int32_t *const items = smem + qa.smem_q_off;
+    uint32_t *const masks = (uint32_t *)(smem + qa.smem_mask_off);   // [slot][buffer][words]
+    int32_t *const spill_base = qa.spill + (int64_t)blockIdx.x * qa.spill_stride;  // [slot][buffer][vmax]
+
+    if (tid < 3) {
+        s_res[tid] = 0u;
+        s_spill[tid][0] = 0;
+        s_spill[tid][1] = 0;
+    }
+    // Per slot (uniform over the block): query, rounds, items and spilled stops
+    // queued for the coming round, and whether the slot must take a new query.
+    int32_t qs[kSlots], rr[kSlots], ni[kSlots], ns[kSlots];
+    bool vq[kSlots], need[kSlots], fresh[kSlots];
+#pragma unroll
+    for (int j = 0; j < kSlots; ++j) {
+        qs[j] = -1;
+        rr[j] = ni[j] = ns[j] = 0;
+        vq[j] = false;
+        need[j] = true;
+        fresh[j] = true;       // the first query of slot j is j * grid + block
+    }
+    int32_t R = 0;             // block round: round R writes buffer R & 1
+    int cs = 0;                // counter slot written this round
+
+    for (;;) {
+        if (need[0] || need[1]) {
+            if (COUNT) {   // block totals of the finishing slots' counters
+#pragma unroll
+                for (int j = 0; j < kSlots; ++j) {
+                    if (!need[j] || qs[j] < 0) continue;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) {
+                        unsigned long long x = (unsigned long long)pc.c[j][k];
+                        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                        if ((tid & 31) == 0) atomicAdd(&s_cnt[j][k], x);
+                        pc.c[j][k] = 0;
+                    }
+                }
+                __syncthreads();
+            }
+            // Finish converged (or capped) queries: result row, status, counters.
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) {
+                if (!need[j] || qs[j] < 0) continue;
+                const int32_t q = qs[j];
+                const int64_t off = qa.arr_off ? __ldg(qa.arr_off + q) : (int64_t)q * V;
+                int32_t *const out = qa.arr_out + off;
+                const int32_t *const a = smem + j * vpad;
+                for (int32_t i = tid; i < V; i += nthr) out[i] = load_arr(a, i, true);
+                if (tid == 0) {
+                    if (qa.status)
+                        qa.status[q] = !vq[j] ? EAT_ERR_INVALID
+                                       : (ni[j] + ns[j] > 0 ? EAT_ERR_NO_CONVERGENCE : EAT_OK);
+                    if (COUNT) {
+                        eat_counters r;
+                        r.rounds = rr[j];
+                        r.vertices = (int64_t)s_cnt[j][0];
+                        r.types = (int64_t)s_cnt[j][1];
+                        r.evals = (int64_t)s_cnt[j][2];
+                        r.lookups = (int64_t)s_cnt[j][3];
+                        r.aps = (int64_t)s_cnt[j][4];
+                        r.relaxed = (int64_t)s_cnt[j][5];
+                        qa.counters[q] = r;
+                    }
+                }
+            }
+            if (tid == 0) {
+#pragma unroll
+                for (int j = 0; j < kSlots; ++j) {
+                    if (!need[j]) continue;
+                    const int32_t nq = fresh[j] ? j * (int32_t)gridDim.x + (int32_t)blockIdx.x
+                                                : kSlots * (int32_t)gridDim.x + atomicAdd(qa.work, 1);
+                    s_q[j] = nq < qa.n ? nq : -1;
+                }
+            }
+            __syncthreads();   // result rows read; new queries visible
+            const int rd = (R & 1) ^ 1;                    // buffer the coming round reads
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) {
+                if (!need[j]) continue;
+                need[j] = false;
+                fresh[j] = false;
+                qs[j] = s_q[j];
+                rr[j] = ni[j] = ns[j] = 0;
+                vq[j] = false;
+                if (qs[j] < 0) continue;                   // no query left for this slot
+                // Algorithm 2 for the slot's new query; its source is the one
+                // spilled stop of the coming round.
+                const int32_t s = __ldg(qa.src + qs[j]);
+                const int32_t t_s = __ldg(qa.ts + qs[j]);
+                const int32_t ni_q = qa.net_idx ? __ldg(qa.net_idx + qs[j]) : 0;
+                vq[j] = ni_q == 0 && (unsigned)s < (unsigned)V;
+                int32_t *const a = smem + j * vpad;
+                for (int32_t i = tid; i < V; i += nthr) a[i] = (vq[j] && i == s) ? t_s : kInf;
+                uint32_t *const m = masks + j * 2 * qa.mask_words;
+                for (int32_t i = tid; i < nwords; i += nthr) {
+                    m[i] = 0u;
+                    m[qa.mask_words + i] = 0u;
+                }
+                if (COUNT && tid < 6) s_cnt[j][tid] = 0ull;
+                if (vq[j]) {
+                    if (tid == 0) spill_base[(int64_t)(j * 2 + rd) * qa.vmax] = s;
+                    ns[j] = 1;
+                }
+            }
+            if (qs[0] < 0 && qs[1] < 0) break;
+            __syncthreads();   // slots initialised before the round reads them
+        }
+
+        const int wr = R & 1, rd = wr ^ 1;
+        int32_t *const it_rd = items + rd * icap;
+        int32_t *const it_wr = items + wr * icap;
+        if (tid == 0) {
+            const int nx = cs == 2 ? 0 : cs + 1;
+            s_res[nx] = 0u;
+            s_spill[nx][0] = 0;
+            s_spill[nx][1] = 0;
+        }
+
+        // Relax type t of tail u for slot j (Algorithm 3 with Algorithm 6).
+        auto relax = [&](int j, int32_t e_u, int32_t k, int32_t t) {
+            const int4 *c = N.ce + 2 * ((int64_t)k * N.n_types + t);
+            int4 ca, cb;
+            load_entry(c, ca, cb);
+            int32_t n, x, aps = 0;
+            entry_aps(cb, N.apx, n, x);
+            const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, k), e_u, N.apx, aps);
+            if (COUNT) {
+                pc.add(j, 1, 1);
+                pc.add(j, 3, 1);
+                pc.add(j, 4, aps);
+            }
+            if (tc == kInf) return;
+            if (COUNT) pc.add(j, 2, 1);
+            int32_t *const a = smem + j * vpad;
+            const int32_t v = cb.y;
+            const int32_t cand = tc + (cb.z & 0xffffff);
+            if (cand >= load_arr(a, v, true)) return;
+            const int32_t old = atomicMin(a + v, cand);
+            if (cand >= old) return;
+            if (COUNT) pc.add(j, 5, 1);
+            int32_t d = (int32_t)((uint32_t)cb.z >> 24);
+            if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - cb.w;
+            if (d <= 0) return;
+            uint32_t *const pmask = masks + (j * 2 + wr) * qa.mask_words;
+            const uint32_t bit = 1u << (v & 31);
+            if (atomicOr(pmask + (v >> 5), bit) & bit) return;
+            const uint32_t before = atomicAdd(&s_res[cs], (uint32_t)d << (j ? 16 : 0));
+            const uint32_t lo = before & 0xffffu, hi = before >> 16;
+            if (lo + hi + (uint32_t)d <= (uint32_t)icap) {
+                const int32_t pos = j ? icap - (int32_t)hi - d : (int32_t)lo;
+                const int32_t hv = (v << 16) | cb.w;
+                it_wr[pos] = hv | kFirstItem;
+                for (int32_t jj = 1; jj < d; ++jj) it_wr[pos + jj] = hv + jj;
+            } else {
+                if (lo + hi <= (uint32_t)icap) s_cross[cs] = before;   // the first that failed
+                spill_base[(int64_t)(j * 2 + wr) * qa.vmax + atomicAdd(&s_spill[cs][j], 1)] = v;
+            }
+        };
+
+        // One thread per (stop, type) item; slot 1's items sit at the buffer's end.
+        const int32_t n0 = ni[0], nall = ni[0] + ni[1];
+        const int32_t gap = icap - nall;
+        for (int32_t i = tid; i < nall; i += nthr) {
+            const int j = i >= n0;
+            const int32_t raw = it_rd[j ? i + gap : i];
+            const int32_t u = (raw >> 16) & 0x7fff;
+            if (raw < 0) {
+                atomicAnd(masks + (j * 2 + rd) * qa.mask_words + (u >> 5), ~(1u << (u & 31)));
+                if (COUNT) pc.add(j, 0, 1);
+            }
+            const int32_t e_u = load_arr(smem + j * vpad, u, true);
+            const int32_t k = cluster_slot(N, e_u);
+            if (k >= N.y) {
+                if (COUNT) pc.add(j, 1, 1);
+                continue;
+            }
+            relax(j, e_u, k, raw & 0xffff);
+        }
+        // Spilled stops of both slots: `vw` lanes per stop.
+        const int32_t s0 = ns[0], sall = ns[0] + ns[1];
+        for (int32_t i = sub; i < sall; i += nsub) {
+            const int j = i >= s0;
+            const int32_t u = __ldcg(spill_base + (int64_t)(j * 2 + rd) * qa.vmax + (j ? i - s0 : i));
+            const int32_t beg = __ldg(N.row_ptr + u);
+            const int32_t end = __ldg(N.row_ptr + u + 1);
+            if (lane == 0) {
+                atomicAnd(masks + (j * 2 + rd) * qa.mask_words + (u >> 5), ~(1u << (u & 31)));
+                if (COUNT) pc.add(j, 0, 1);
+            }
+            const int32_t e_u = load_arr(smem + j * vpad, u, true);
+            const int32_t k = cluster_slot(N, e_u);
+            if (k >= N.y) {
+                if (COUNT && lane == 0) pc.add(j, 1, end - beg);
+                continue;
+            }
+            for (int32_t t = beg + lane; t < end; t += vw) relax(j, e_u, k, t);
+        }
+        __syncthreads();
+        const uint32_t res = s_res[cs];
+        const bool over = (res & 0xffffu) + (res >> 16) > (uint32_t)icap;
+        const uint32_t okr = over ? s_cross[cs] : res;
+        const int32_t nn[kSlots] = {(int32_t)(okr & 0xffffu), (int32_t)(okr >> 16)};
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) {
+            if (qs[j] < 0) continue;
+            rr[j] += ni[j] + ns[j] > 0;                    // a round with work for the slot
+            ni[j] = nn[j];
+            ns[j] = s_spill[cs][j];
+            need[j] = ni[j] + ns[j] == 0 || rr[j] >= qa.max_rounds;
+        }
+        cs = cs == 2 ? 0 : cs + 1;
+        ++R;
+    }
+}
+
 // ------------------------------------------------------------------ asynchronous mode
 //
 // The same fixpoint without rounds.  The frontier is a bitmap of pending stops in
@@ -311,7 +580,7 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
         const int q = s_q;
         if (q >= qa.n) break;
 
-        const int ni = (NETS == 1 || qa.net_idx == nullptr) ? 0 : __ldg(qa.net_idx + q);
+        const int ni = qa.net_idx == nullptr ? 0 : __ldg(qa.net_idx + q);
         const bool net_ok = (unsigned)ni < (unsigned)qa.n_nets;
         const NetDev &N = nets.net[net_ok ? ni : 0];
         const int32_t V = N.n_stops;
@@ -549,7 +818,7 @@ eat_cluster_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs 
     }
     const int32_t s = __ldg(qa.src + q);
     const int32_t t_s = __ldg(qa.ts + q);
-    const bool valid = (unsigned)s < (unsigned)V;
+    const bool valid = (qa.net_idx == nullptr || __ldg(qa.net_idx + q) == 0) && (unsigned)s < (unsigned)V;
     __syncthreads();
     // The source is the frontier of "round -1" in the block that holds it.
     if (tid == 0 && valid && s % C == me) {
@@ -774,6 +1043,19 @@ cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int 
     }
     if (n_nets == 1) return launch_cta_t<1>(nets, n_nets, qa, mem, grid, block, smem, st);
     return launch_cta_t<EAT_MAX_NETS>(nets, n_nets, qa, mem, grid, block, smem, st);
+}
+
+const void *pair_kernel(bool count) {
+    return count ? (const void *)eat_pair_kernel<true> : (const void *)eat_pair_kernel<false>;
+}
+
+cudaError_t launch_pair(const NetDev &net, const QueryArgs &qa, int grid, int block, size_t smem,
+                        cudaStream_t st) {
+    NetTable<1> tab;
+    tab.net[0] = net;
+    if (qa.counters) eat_pair_kernel<true><<<grid, block, smem, st>>>(tab, qa);
+    else eat_pair_kernel<false><<<grid, block, smem, st>>>(tab, qa);
+    return cudaGetLastError();
 }
 
 const void *cluster_kernel() { return (const void *)eat_cluster_kernel<1>; }

@@ -52,6 +52,13 @@ cudaError_t launch_async(const NetDev *nets, int n_nets, const QueryArgs &qa, in
 const void *cluster_kernel();
 cudaError_t launch_cluster(const NetDev &net, const QueryArgs &qa, int cluster, int grid,
                            int block, size_t smem, cudaStream_t st);
+// Paired mode: two queries per block on one network of at most 32,767 stops and
+// 65,535 types; both arrival rows and bitmaps in shared memory (smem_arr_cap = ints
+// per row, bitmaps [slot][buffer]), spill queues [slot][buffer][vmax] per block;
+// count: the instantiation that fills qa.counters.
+const void *pair_kernel(bool count = false);
+cudaError_t launch_pair(const NetDev &net, const QueryArgs &qa, int grid, int block, size_t smem,
+                        cudaStream_t st);
 cudaError_t launch_next_departure(const NetDev &N, const int32_t *types, const int32_t *times,
                                   int32_t n, int32_t *out, cudaStream_t st);
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libeat.so")
 EAT_INF = 2**31 - 1
 EAT_OK, EAT_ERR_INVALID, EAT_ERR_OOM, EAT_ERR_CUDA = 0, 1, 2, 3
 EAT_ERR_NO_CONVERGENCE, EAT_ERR_NO_DEVICE, EAT_ERR_WORKSPACE = 4, 5, 6
-EAT_MODE_AUTO, EAT_MODE_CTA, EAT_MODE_CLUSTER, EAT_MODE_ASYNC = 0, 1, 2, 3
+EAT_MODE_AUTO, EAT_MODE_CTA, EAT_MODE_CLUSTER, EAT_MODE_ASYNC, EAT_MODE_PAIR = 0, 1, 2, 3, 4
 EAT_PLACE_AUTO, EAT_PLACE_SHARED, EAT_PLACE_GLOBAL_ARR, EAT_PLACE_GLOBAL = 0, 1, 2, 3
 EAT_SUBTRIPS_NONE, EAT_SUBTRIPS_SQRT_K, EAT_SUBTRIPS_SQRT_MEAN = 0, 1, 2
 EAT_MAX_NETS = 128
@@ -121,6 +121,8 @@ _sig("eat_net_host_view", ctypes.c_int, [_vp, ctypes.POINTER(eat_net_view)])
 _sig("eat_query", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp])
 _sig("eat_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(_vp), ctypes.c_int32,
                                               ctypes.c_int32, ctypes.POINTER(eat_query_opts)])
+_sig("eat_launch_shape", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(eat_query_opts), ctypes.POINTER(eat_query_opts)])
 _sig("eat_query_batch", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_size_t,
                                        ctypes.POINTER(eat_query_opts), _vp])
 _sig("eat_query_batch_multi", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, _vp, _vp, _vp,
@@ -162,7 +164,7 @@ _sig("eat_ladder_host_view", ctypes.c_int, [_vp, ctypes.POINTER(eat_ladder_view)
 
 EXPORTED = ("eat_autotune", "eat_server_create", "eat_server_submit", "eat_server_poll", "eat_server_get_stats",
             "eat_server_destroy", "eat_last_error", "eat_version", "eat_build", "eat_build_csr", "eat_free", "eat_get_stats",
-            "eat_net_host_view", "eat_query", "eat_workspace_bytes", "eat_query_batch",
+            "eat_net_host_view", "eat_query", "eat_workspace_bytes", "eat_launch_shape", "eat_query_batch",
             "eat_query_batch_multi", "eat_next_departure", "eat_query_batch_noalloc",
             "eat_ladder_build", "eat_ladder_free", "eat_ladder_query", "eat_ladder_host_view")
 
@@ -329,6 +331,18 @@ def eat_workspace_bytes(nets, n, **opts) -> int:
     arr = (_vp * len(nets))(*[x.handle.value for x in nets])
     o = _opts(**opts)
     return int(_lib.eat_workspace_bytes(arr, len(nets), int(n), ctypes.byref(o)))
+
+
+def eat_launch_shape(nets, n, **opts) -> dict:
+    """Launch shape a batch of n queries would run with: block, vwarp, mode, cluster."""
+    if isinstance(nets, Net):
+        nets = [nets]
+    arr = (_vp * len(nets))(*[x.handle.value for x in nets])
+    o = _opts(**opts)
+    shape = eat_query_opts()
+    _check(_lib.eat_launch_shape(arr, len(nets), int(n), ctypes.byref(o), ctypes.byref(shape)),
+           "eat_launch_shape")
+    return {"block": shape.block, "vwarp": shape.vwarp, "mode": shape.mode, "cluster": shape.cluster}
 
 
 def eat_query_batch(net: Net, sources, times, out, workspace=None, workspace_bytes=None,
