@@ -338,9 +338,10 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     const int place = o ? o->placement : EAT_PLACE_AUTO;
     if (place < EAT_PLACE_AUTO || place > EAT_PLACE_GLOBAL)
         return fail(EAT_ERR_INVALID, "placement must be one of EAT_PLACE_*");
-    // More queries than SMs on one network of 8,192 to 32,767 stops: two queries per
-    // 1,024-thread block (a block whose query converges early gives its threads to the
-    // other one), unless a tuned shape or an explicit block size says otherwise.  On
+    // More queries than SMs on one network of 8,192 stops or more whose two arrival rows
+    // fit a block's shared memory: two queries per 1,024-thread block (a block whose
+    // query converges early gives its threads to the other one), unless a tuned shape or
+    // an explicit block size says otherwise.  On
     // smaller networks a round carries too few items for the shared threads to pay for
     // running two queries in lockstep (measured: 20,000 stops 4.7 % faster per
     // 256-query batch, 1,024 stops 24 % slower).

@@ -50,6 +50,12 @@ int main(void) {
     CHECK(eat_query(net, 0, 28800, row, NULL) == EAT_ERR_NO_DEVICE);
     CHECK(strlen(eat_last_error()) > 0);
 
+    const eat_net *nets[1] = {net};
+    eat_query_opts shape;
+    CHECK(eat_launch_shape(nets, 1, 8, NULL, &shape) == EAT_ERR_NO_DEVICE);
+    CHECK(eat_launch_shape(nets, 1, 8, NULL, NULL) == EAT_ERR_INVALID);
+    CHECK(eat_launch_shape(nets, 0, 8, NULL, &shape) == EAT_ERR_INVALID);
+
     eat_ladder *lad = NULL;
     CHECK(eat_ladder_build(&c, &o, &lad) == EAT_OK && lad != NULL);
     eat_ladder_view lv;
