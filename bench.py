@@ -335,7 +335,7 @@ def describe(name, tt, batch):
                  "stops, headway 3-30 min, 10% jittered trips, 3 duration bands",
     }[name]
     return {"workload": desc, "global_batch": batch, "n_stops": int(tt.n_stops),
-            "method": "Cluster-AP fixpoint (one thread block per query)",
+            "method": "Cluster-AP fixpoint, rounds inside one launch (launch_shape gives the kernel)",
             "n_connections": int(tt.n_conn), "times": "int32 seconds",
             "l2": "flushed before every step (256 MB write)", "parallelism": "replicas"}
 
