@@ -161,14 +161,17 @@ typedef struct {
     int32_t max_rounds;      /* round cap; 0 = n_stops + 1 (always enough: every
                                 productive round fixes at least one more stop) */
     int32_t block;           /* threads per CTA: 0 = automatic (the tuned shape, else 1024
-                                when the batch has at most one query per SM or runs in
-                                the paired mode, else 512);
+                                when the batch has at most one query per SM, runs in the
+                                paired mode or is on a network of 8,192 stops or more,
+                                else 512);
                                 else 64..1024, multiple of 32 */
     int32_t vwarp;           /* lanes per active stop (1, 2, 4, 8, 16 or 32); 0 = automatic */
     int32_t mode;            /* EAT_MODE_* */
     int32_t placement;       /* EAT_PLACE_*: where a query's arrivals and frontier
                                 bitmap live; 0 = automatic */
     int32_t cluster;         /* blocks per query in EAT_MODE_CLUSTER: 2, 4 or 8; 0 = 8 */
+    int32_t order;           /* EAT_ORDER_*: the order in which a batch's queries start;
+                                0 = automatic */
     int32_t *status;         /* optional [n] per-query eat_status, device memory */
     eat_counters *counters;  /* optional [n] per-query counters, device memory */
 } eat_query_opts;
@@ -179,6 +182,23 @@ enum eat_placement {
                                     4 * n_stops + n_stops / 8 bytes to fit a CTA) */
     EAT_PLACE_GLOBAL_ARR = 2,    /* arrivals in the output row, bitmap in shared memory */
     EAT_PLACE_GLOBAL = 3         /* arrivals and bitmap in global memory */
+};
+
+enum eat_order {
+    EAT_ORDER_AUTO = 0,      /* EAT_ORDER_BY_TIME when the batch has more queries than
+                                the launch runs at once (some wait for a free block) or
+                                runs in EAT_MODE_PAIR, else EAT_ORDER_AS_GIVEN */
+    EAT_ORDER_BY_TIME = 1,   /* queries start in order of departure time t_s (15-minute
+                                buckets, earliest first; a one-block device counting sort
+                                before the launch, n int32 of workspace): the longest
+                                queries start first, and queries running at the same time
+                                read the same clusters of the network from L2 (measured:
+                                large network 17.8 -> 14.0 ms per 1,024-query step, city
+                                0.88 -> 0.70 ms per 256-query step with one 1,024-thread
+                                block per query).  Results, status and counters stay at
+                                each query's index */
+    EAT_ORDER_AS_GIVEN = 2   /* queries start in index order (always in
+                                eat_query_batch_noalloc and for a single query) */
 };
 
 enum eat_mode {
@@ -201,10 +221,9 @@ enum eat_mode {
                            network of at most 32,767 stops and 65,535 connection types
                            whose two arrival rows fit in one block's shared memory: when
                            one query converges its threads go to the other and the slot
-                           takes the next query.  EAT_MODE_AUTO picks it (unless a tuned
-                           shape or opts->block says otherwise) for batches of more
-                           queries than SMs on one network of 8,192 stops or more; never
-                           automatically in eat_query_batch_noalloc */
+                           takes the next query.  EAT_MODE_AUTO uses it only where
+                           eat_autotune chose it; never in eat_query_batch_noalloc
+                           unless requested */
 };
 
 /* Error message of the calling thread's last failed call ("" if none). */
@@ -388,9 +407,10 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
  * sweeps the virtual-warp size by hand, Section V-B).  Candidates, in this
  * order: block sizes 512, 1024 and 256 threads, each with the round-based mode
  * and vwarp 8, 4, 16, 2, 32 lanes per spilled stop, then with the asynchronous
- * mode, as far as they fit the device; when n exceeds the SM count, also the
- * paired mode with vwarp 8, 4 and 16 (placed first on networks of 8,192 stops or
- * more, where it is the default, else last).  They are run on the sample batch
+ * mode, as far as they fit the device (1024 threads first on networks of 8,192
+ * stops or more and for batches of at most one query per SM, where it is the
+ * default); when n exceeds the SM count, then the paired mode with vwarp 8, 4
+ * and 16.  They are run on the sample batch
  * sources/times (n queries, device memory) in nine rounds over all candidates:
  * the first warms up, the other eight are timed with CUDA events on `stream`,
  * each after a write of twice the L2 size so that every timing starts with the

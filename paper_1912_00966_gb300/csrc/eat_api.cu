@@ -127,6 +127,8 @@ struct Plan {
     int cluster = 0;              // blocks per query in cluster mode (EAT_MODE_CLUSTER), else 0
     bool pack = false;            // one int32 per queued item (small networks, shared arrivals)
     bool pair = false;            // two queries per block (EAT_MODE_PAIR)
+    bool order = false;           // queries start by t_s (EAT_ORDER_BY_TIME): order array at off_order
+    size_t off_order = 0;
 };
 
 static constexpr size_t kWsHeader = 256;   // work counter + internal status / counters
@@ -241,7 +243,7 @@ static int make_cluster_plan(int dev, const DeviceInfo &d, int32_t vmax, int32_t
     return EAT_OK;
 }
 
-static constexpr int32_t kPairMinStops = 8192;   // automatic paired mode from this size
+static constexpr int32_t kWideMinStops = 8192;   // 1,024-thread blocks for any batch from this size
 
 // Plan of the paired kernel: two arrival rows, four bitmaps (two per query) and the
 // shared item buffers (one int32 per item) in one block's shared memory.  Returns
@@ -286,9 +288,8 @@ static int make_pair_plan(int dev, const DeviceInfo &d, int32_t vmax, int32_t n,
     return EAT_OK;
 }
 
-static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_query_opts *o,
-                     Plan &p, int32_t vmin = -1, const eat_net *tuned = nullptr,
-                     bool own_workspace = true) {
+static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const eat_query_opts *o,
+                          Plan &p, int32_t vmin, const eat_net *tuned, bool own_workspace) {
     if (vmin < 0) vmin = vmax;
     DeviceInfo d;
     int rc = device_info(dev, d);
@@ -304,10 +305,14 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
         tv = (int)((sh >> 16) & 0xffu);
         tm = (int)(sh >> 24);
     }
-    // Default shape: with at most one query per SM each query gets a 1,024-thread
-    // block (measured faster for single queries and small batches); fuller batches
-    // run two 512-thread blocks per SM unless a tuned shape says otherwise.
-    p.block = (o && o->block) ? o->block : (tb ? tb : (n >= 1 && n <= d.sms ? 1024 : 512));
+    // Default shape: a 1,024-thread block per query when the batch has at most one query
+    // per SM, or on networks of 8,192 stops or more (there the batch starts in order of
+    // t_s, so the longest queries run first and the later ones fill the blocks that
+    // free up: city 0.70 ms per 256-query step against 0.88 ms for two 512-thread
+    // blocks per SM); fuller batches on small networks run two 512-thread blocks per SM.
+    // A tuned shape or opts->block overrides.
+    p.block = (o && o->block) ? o->block
+              : (tb ? tb : (n >= 1 && (n <= d.sms || vmax >= kWideMinStops) ? 1024 : 512));
     if (p.block < 64 || p.block > 1024 || p.block % 32)
         return fail(EAT_ERR_INVALID, "block must be a multiple of 32 in 64..1024");
     int vw = (o && o->vwarp) ? o->vwarp : (tv ? tv : 8);
@@ -338,19 +343,15 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     const int place = o ? o->placement : EAT_PLACE_AUTO;
     if (place < EAT_PLACE_AUTO || place > EAT_PLACE_GLOBAL)
         return fail(EAT_ERR_INVALID, "placement must be one of EAT_PLACE_*");
-    // More queries than SMs on one network of 8,192 stops or more whose two arrival rows
-    // fit a block's shared memory: two queries per 1,024-thread block (a block whose
-    // query converges early gives its threads to the other one), unless a tuned shape or
-    // an explicit block size says otherwise.  On
-    // smaller networks a round carries too few items for the shared threads to pay for
-    // running two queries in lockstep (measured: 20,000 stops 4.7 % faster per
-    // 256-query batch, 1,024 stops 24 % slower).
+    // The paired mode when the autotuner chose it for this batch size (never by default:
+    // with the batch started in order of t_s, one query per 1,024-thread block is faster
+    // on the city network, 0.70 against 0.79 ms per 256-query step).
     const bool explicit_block = o && o->block;
     if ((!o || o->mode == EAT_MODE_AUTO) && own_workspace && n_nets == 1 && tuned &&
         (place == EAT_PLACE_AUTO || place == EAT_PLACE_SHARED) && !explicit_block &&
-        (tm == EAT_MODE_PAIR || (tm == 0 && n > d.sms && vmax >= kPairMinStops))) {
+        tm == EAT_MODE_PAIR) {
         Plan q = p;
-        q.block = tm == EAT_MODE_PAIR && tb ? tb : 1024;
+        q.block = tb ? tb : 1024;
         if (make_pair_plan(dev, d, vmax, n, tuned, q) == EAT_OK) {
             p = q;
             return EAT_OK;
@@ -438,6 +439,29 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
     return EAT_OK;
 }
 
+// Launch plan for n queries; with a workspace of its own, a batch of more than one query
+// also gets its start order (EAT_ORDER_BY_TIME) at the end of the workspace.
+static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_query_opts *o,
+                     Plan &p, int32_t vmin = -1, const eat_net *tuned = nullptr,
+                     bool own_workspace = true) {
+    const int order = o ? o->order : EAT_ORDER_AUTO;
+    if (order < EAT_ORDER_AUTO || order > EAT_ORDER_AS_GIVEN)
+        return fail(EAT_ERR_INVALID, "order must be one of EAT_ORDER_*");
+    int rc = make_plan_core(dev, vmax, n, n_nets, o, p, vmin < 0 ? vmax : vmin, tuned, own_workspace);
+    if (rc) return rc;
+    // Automatic: sorted when some queries must wait for a free block (they then start
+    // longest first) and in the paired mode (an early query shares its block with a
+    // late one); a batch that starts all at once gains nothing for the sort's launch.
+    const bool waits = p.cluster == 0 && !p.pair && n > p.grid;
+    if (own_workspace && n > 1 &&
+        (order == EAT_ORDER_BY_TIME || (order == EAT_ORDER_AUTO && (waits || p.pair)))) {
+        p.order = true;
+        p.off_order = align_up(p.ws_bytes, 256);
+        p.ws_bytes = p.off_order + align_up((size_t)n * 4, 256);
+    }
+    return EAT_OK;
+}
+
 // Kernel arguments for a plan; `grid` persistent blocks share the scratch at `ws`.
 static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net_idx,
                            const int32_t *src, const int32_t *ts, int32_t n, int n_nets,
@@ -468,6 +492,7 @@ static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net
     qa.smem_arr_cap = p.smem_arr_cap;
     qa.arr_rows = nullptr;
     qa.arr_rows_stride = 0;
+    qa.order = p.order ? (const int32_t *)(ws + p.off_order) : nullptr;
     return qa;
 }
 
@@ -523,6 +548,10 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
     DeviceGuard guard(dev);
     cudaError_t e = cudaMemsetAsync(qa.work, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (p.order) {
+        e = launch_order(ts, n, (int32_t *)((char *)ws + p.off_order), st);
+        if (e != cudaSuccess) return cuda_fail(e, "start-order kernel launch");
+    }
     NetDev devs[EAT_MAX_NETS];
     for (int i = 0; i < n_nets; ++i) devs[i] = nets[i]->dev;
     e = p.cluster ? launch_cluster(devs[0], qa, p.cluster, p.grid, p.block, p.smem, st)
@@ -1014,9 +1043,8 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
         std::vector<float> ms;
     };
     std::vector<Cand> cands;
-    // Fixed order, the library's default shape first (two queries per 1,024-thread
-    // block when make_plan would pick them, else 512 threads, vwarp 8, rounds): ties
-    // below go to the earliest.
+    // Fixed order, the library's default shape first (rounds, vwarp 8, 1,024 threads on
+    // networks of 8,192 stops or more, else 512): ties below go to the earliest.
     DeviceInfo dinfo;
     int drc = device_info(net->device, dinfo);
     if (drc) return drc;
@@ -1028,9 +1056,8 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
             for (int v : {8, 4, 16}) pairs.push_back({EAT_MODE_PAIR, 1024, v, {}});
         else clear_error();                  // network too large for two rows per block
     }
-    const bool pairs_first = net->host.n_stops >= kPairMinStops;
-    if (pairs_first) cands = pairs;
-    for (int b : {512, 1024, 256}) {
+    const bool wide = net->host.n_stops >= kWideMinStops || n <= dinfo.sms;
+    for (int b : {wide ? 1024 : 512, wide ? 512 : 1024, 256}) {
         for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, {}});
         eat_query_opts o{};
         o.block = b;
@@ -1039,7 +1066,7 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
         if (eat_workspace_bytes(nets, 1, n, &o)) cands.push_back({EAT_MODE_ASYNC, b, 8, {}});
         else clear_error();                  // bitmap does not fit: not a candidate
     }
-    if (!pairs_first) cands.insert(cands.end(), pairs.begin(), pairs.end());
+    cands.insert(cands.end(), pairs.begin(), pairs.end());
     size_t ws_need = 0;
     std::vector<Cand> usable;                // shapes that have a plan on this device
     for (const Cand &cd : cands) {

@@ -53,6 +53,13 @@ __device__ __forceinline__ int32_t load_arr(const int32_t *arr, int32_t i, bool 
     return __ldcg(arr + i);
 }
 
+// Index of the next query a persistent block takes: the work counter's next value,
+// through the start order when there is one (values >= n end the block's loop).
+__device__ __forceinline__ int32_t next_query(const QueryArgs &qa) {
+    const int32_t w = atomicAdd(qa.work, 1);
+    return (qa.order && w < qa.n) ? __ldg(qa.order + w) : w;
+}
+
 constexpr int32_t kNullItem = -1;           // hole left by a stop that spilled
 constexpr int32_t kFirstItem = INT32_MIN;    // flag on the first item of a stop
 
@@ -84,7 +91,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                                           : qa.gmask + (int64_t)blockIdx.x * qa.mask_stride;
 
     for (;;) {
-        if (tid == 0) s_q = atomicAdd(qa.work, 1);
+        if (tid == 0) s_q = next_query(qa);
         if (tid < 6) s_cnt[tid] = 0;
         __syncthreads();
         const int q = s_q;
@@ -393,9 +400,9 @@ eat_pair_kernel(const __grid_constant__ NetTable<1> nets, const QueryArgs qa) {
 #pragma unroll
                 for (int j = 0; j < kSlots; ++j) {
                     if (!need[j]) continue;
-                    const int32_t nq = fresh[j] ? j * (int32_t)gridDim.x + (int32_t)blockIdx.x
-                                                : kSlots * (int32_t)gridDim.x + atomicAdd(qa.work, 1);
-                    s_q[j] = nq < qa.n ? nq : -1;
+                    const int32_t w = fresh[j] ? j * (int32_t)gridDim.x + (int32_t)blockIdx.x
+                                               : kSlots * (int32_t)gridDim.x + atomicAdd(qa.work, 1);
+                    s_q[j] = w >= qa.n ? -1 : qa.order ? __ldg(qa.order + w) : w;
                 }
             }
             __syncthreads();   // result rows read; new queries visible
@@ -574,7 +581,7 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
                    *const st_k = stage + 96;
 
     for (;;) {
-        if (tid == 0) s_q = atomicAdd(qa.work, 1);
+        if (tid == 0) s_q = next_query(qa);
         if (tid < 6) s_cnt[tid] = 0;
         __syncthreads();
         const int q = s_q;
@@ -743,6 +750,63 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
     }
 }
 
+// Start order of a batch: a counting sort of the query indices by t_s in 15-minute
+// buckets (earliest first) in one block.  Queries started together then look up the
+// same clusters of the network, and the longest (earliest) start first.
+constexpr int kOrderBuckets = 4096;          // 15-minute buckets: 42 days
+constexpr int kOrderThreads = 1024;
+
+__device__ __forceinline__ int order_bucket(int32_t t) {
+    return t <= 0 ? 0 : min(t / 900, kOrderBuckets - 1);
+}
+
+__global__ void __launch_bounds__(kOrderThreads)
+eat_order_kernel(const int32_t *__restrict__ ts, int32_t n, int32_t *__restrict__ order) {
+    __shared__ int32_t hist[kOrderBuckets];
+    __shared__ int32_t wsum[kOrderThreads / 32];
+    constexpr int kPer = kOrderBuckets / kOrderThreads;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int b = tid; b < kOrderBuckets; b += kOrderThreads) hist[b] = 0;
+    __syncthreads();
+    for (int32_t i = tid; i < n; i += kOrderThreads) atomicAdd(&hist[order_bucket(__ldg(ts + i))], 1);
+    __syncthreads();
+    // Exclusive prefix sum: thread tid owns buckets [kPer * tid, kPer * tid + kPer).
+    int32_t loc[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        loc[k] = hist[kPer * tid + k];
+        sum += loc[k];
+    }
+    int32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int32_t base = x - sum + (warp ? wsum[warp - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        hist[kPer * tid + k] = base;
+        base += loc[k];
+    }
+    __syncthreads();
+    for (int32_t i = tid; i < n; i += kOrderThreads)
+        order[atomicAdd(&hist[order_bucket(__ldg(ts + i))], 1)] = i;
+}
+
 __global__ void eat_next_departure_kernel(const NetDev N, const int32_t *types,
                                           const int32_t *times, int32_t n, int32_t *out) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -777,7 +841,8 @@ eat_cluster_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs 
 
     const int C = (int)cluster.num_blocks();
     const int me = (int)cluster.block_rank();
-    const int q = blockIdx.x / C;                     // the same for the whole cluster
+    const int qi = blockIdx.x / C;                    // the same for the whole cluster
+    const int q = (qa.order && qi < qa.n) ? __ldg(qa.order + qi) : qi;
     if (q >= qa.n) return;
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -1077,6 +1142,12 @@ cudaError_t launch_cluster(const NetDev &net, const QueryArgs &qa, int cluster, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, eat_cluster_kernel<1>, tab, qa);
+}
+
+cudaError_t launch_order(const int32_t *ts, int32_t n, int32_t *order, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    eat_order_kernel<<<1, kOrderThreads, 0, st>>>(ts, n, order);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_next_departure(const NetDev &N, const int32_t *types, const int32_t *times,

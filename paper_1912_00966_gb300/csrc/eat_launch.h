@@ -33,6 +33,7 @@ struct QueryArgs {
     int32_t *arr_rows;         // [grid][arr_rows_stride]: a block's arrivals when they are not
                                // in shared memory and arr_out is host memory, or nullptr
     int64_t arr_rows_stride;   // ints per block row
+    const int32_t *order;      // [n]: the i-th query handed out is order[i], or nullptr (i)
 };
 
 // mem: 0 = arrivals and bitmaps in shared memory, 1 = arrivals global / bitmaps
@@ -59,6 +60,9 @@ cudaError_t launch_cluster(const NetDev &net, const QueryArgs &qa, int cluster, 
 const void *pair_kernel(bool count = false);
 cudaError_t launch_pair(const NetDev &net, const QueryArgs &qa, int grid, int block, size_t smem,
                         cudaStream_t st);
+// order[0..n) = query indices sorted by t_s (15-minute buckets, earliest first; one
+// block, counting sort; the order inside a bucket is not fixed).
+cudaError_t launch_order(const int32_t *ts, int32_t n, int32_t *order, cudaStream_t st);
 cudaError_t launch_next_departure(const NetDev &N, const int32_t *types, const int32_t *times,
                                   int32_t n, int32_t *out, cudaStream_t st);
 

@@ -19,6 +19,7 @@ EAT_INF = 2**31 - 1
 EAT_OK, EAT_ERR_INVALID, EAT_ERR_OOM, EAT_ERR_CUDA = 0, 1, 2, 3
 EAT_ERR_NO_CONVERGENCE, EAT_ERR_NO_DEVICE, EAT_ERR_WORKSPACE = 4, 5, 6
 EAT_MODE_AUTO, EAT_MODE_CTA, EAT_MODE_CLUSTER, EAT_MODE_ASYNC, EAT_MODE_PAIR = 0, 1, 2, 3, 4
+EAT_ORDER_AUTO, EAT_ORDER_BY_TIME, EAT_ORDER_AS_GIVEN = 0, 1, 2
 EAT_PLACE_AUTO, EAT_PLACE_SHARED, EAT_PLACE_GLOBAL_ARR, EAT_PLACE_GLOBAL = 0, 1, 2, 3
 EAT_SUBTRIPS_NONE, EAT_SUBTRIPS_SQRT_K, EAT_SUBTRIPS_SQRT_MEAN = 0, 1, 2
 EAT_MAX_NETS = 128
@@ -82,7 +83,7 @@ class eat_query_opts(ctypes.Structure):
     _fields_ = [("max_rounds", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("vwarp", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("placement", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("status", _vp), ("counters", _vp)]
+                ("order", ctypes.c_int32), ("status", _vp), ("counters", _vp)]
 
 
 class eat_server_opts(ctypes.Structure):
@@ -307,10 +308,10 @@ def eat_net_host_view(net: Net) -> dict:
     }
 
 
-def _opts(max_rounds=0, block=0, vwarp=0, mode=0, placement=0, cluster=0, status=None,
+def _opts(max_rounds=0, block=0, vwarp=0, mode=0, placement=0, cluster=0, order=0, status=None,
           counters=None):
     return eat_query_opts(int(max_rounds), int(block), int(vwarp), int(mode), int(placement),
-                          int(cluster), _ptr(status), _ptr(counters))
+                          int(cluster), int(order), _ptr(status), _ptr(counters))
 
 
 def eat_query(net: Net, s: int, t_s: int, out=None, counters: bool = False):

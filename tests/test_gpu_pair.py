@@ -154,16 +154,17 @@ def test_rejected_where_not_available(eat, small):
         eat.eat_query_batch(net, _dev([0]), _dev([30000]), outb, mode=PAIR)
 
 
-def test_launch_shape_picks_pairs_for_large_batches(eat, small, city):
-    """Automatic shape: two queries per block once a batch has more queries than SMs on
-    one network of 8,192 to 32,767 stops; the per-query kernel otherwise."""
+def test_launch_shape_defaults(eat, small, city):
+    """Automatic shape: one 1,024-thread block per query for batches of at most one query
+    per SM and on networks of 8,192 stops or more, two 512-thread blocks per SM for larger
+    batches on small networks; the paired mode only when asked for (or tuned)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert eat.eat_launch_shape(city.net, sms + 1)["mode"] == PAIR
-    assert eat.eat_launch_shape(city.net, sms + 1)["block"] == 1024
-    assert eat.eat_launch_shape(small.net, sms + 1)["mode"] == 1       # 1,024 stops
+    assert eat.eat_launch_shape(city.net, sms + 1) == {"block": 1024, "vwarp": 8, "mode": 1, "cluster": 0}
+    assert eat.eat_launch_shape(small.net, sms + 1)["block"] == 512
     assert eat.eat_launch_shape(small.net, sms + 1, mode=PAIR)["mode"] == PAIR
+    assert eat.eat_launch_shape(city.net, sms + 1, mode=PAIR)["block"] == 1024
     for case in (small, city):
-        assert eat.eat_launch_shape(case.net, sms)["mode"] == 1
+        assert eat.eat_launch_shape(case.net, sms) == {"block": 1024, "vwarp": 8, "mode": 1, "cluster": 0}
         assert eat.eat_launch_shape(case.net, 4 * sms, block=512)["mode"] == 1
         assert eat.eat_launch_shape(case.net, 4 * sms, mode=3)["mode"] == 3
     other = eat.eat_build(small.tt.n_stops, small.tt.u, small.tt.v, small.tt.dep, small.tt.dur,
@@ -177,8 +178,8 @@ def test_launch_shape_picks_pairs_for_large_batches(eat, small, city):
 
 
 def test_default_batch_and_autotune(eat, city):
-    """The default call on a batch larger than the SM count runs paired; the tuner may
-    keep that or pick another shape, and results stay the oracle's."""
+    """The default call on a batch larger than the SM count (started in order of t_s) and
+    the shape the tuner picks, paired or not, give the oracle's results."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     n = sms + 40
     q = synth.random_queries(city.tt, n, 0xA9)
@@ -218,3 +219,21 @@ def test_multi_entry_point_one_network(eat, small, mode):
     assert (st[ok] == 0).all() and (st[~ok] == eat.EAT_ERR_INVALID).all()
     assert np.array_equal(rows[ok], small.oracle_rows(q.source[ok], q.t_s[ok]))
     assert (rows[~ok] == 2**31 - 1).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 3, PAIR])
+def test_start_order_keeps_results_in_place(eat, city, mode):
+    """Queries start in order of t_s by default (a device sort of the batch) or as given;
+    rows, status and counters stay at each query's index either way."""
+    q = synth.random_queries(city.tt, 300, 0xAB)
+    want = city.oracle_rows(q.source, q.t_s)
+    by_time, st0, c0 = city.run(eat, q.source, q.t_s, mode=mode)
+    as_given, st1, c1 = city.run(eat, q.source, q.t_s, mode=mode, order=eat.EAT_ORDER_AS_GIVEN)
+    assert (st0 == 0).all() and (st1 == 0).all()
+    assert np.array_equal(by_time, want) and np.array_equal(as_given, want)
+    relaxed_floor = (want < 2**31 - 1).sum(axis=1) - 1
+    assert (c0[:, 6] >= relaxed_floor).all() and (c1[:, 6] >= relaxed_floor).all()
+    n_ws = eat.eat_workspace_bytes(city.net, 300, mode=mode)
+    assert n_ws >= eat.eat_workspace_bytes(city.net, 300, mode=mode, order=eat.EAT_ORDER_AS_GIVEN) + 1200
+    with pytest.raises(eat.EatError):
+        city.run(eat, q.source[:4], q.t_s[:4], order=7)
