@@ -162,7 +162,7 @@ typedef struct {
                                 productive round fixes at least one more stop) */
     int32_t block;           /* threads per CTA: 0 = automatic (the tuned shape, else 1024
                                 when the batch has at most one query per SM, runs in the
-                                paired mode or is on a network of 8,192 stops or more,
+                                paired mode or is on one network of 8,192 stops or more,
                                 else 512);
                                 else 64..1024, multiple of 32 */
     int32_t vwarp;           /* lanes per active stop (1, 2, 4, 8, 16 or 32); 0 = automatic */
@@ -185,9 +185,10 @@ enum eat_placement {
 };
 
 enum eat_order {
-    EAT_ORDER_AUTO = 0,      /* EAT_ORDER_BY_TIME when the batch has more queries than
-                                the launch runs at once (some wait for a free block) or
-                                runs in EAT_MODE_PAIR, else EAT_ORDER_AS_GIVEN */
+    EAT_ORDER_AUTO = 0,      /* on one network: EAT_ORDER_BY_TIME when the batch has more
+                                queries than the launch runs at once (some wait for a
+                                free block) or runs in EAT_MODE_PAIR; otherwise, and for
+                                batches over several networks, EAT_ORDER_AS_GIVEN */
     EAT_ORDER_BY_TIME = 1,   /* queries start in order of departure time t_s (15-minute
                                 buckets, earliest first; a one-block device counting sort
                                 before the launch, n int32 of workspace): the longest

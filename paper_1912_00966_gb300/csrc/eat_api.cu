@@ -306,13 +306,16 @@ static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const ea
         tm = (int)(sh >> 24);
     }
     // Default shape: a 1,024-thread block per query when the batch has at most one query
-    // per SM, or on networks of 8,192 stops or more (there the batch starts in order of
-    // t_s, so the longest queries run first and the later ones fill the blocks that
+    // per SM, or on one network of 8,192 stops or more (there the batch starts in order
+    // of t_s, so the longest queries run first and the later ones fill the blocks that
     // free up: city 0.70 ms per 256-query step against 0.88 ms for two 512-thread
-    // blocks per SM); fuller batches on small networks run two 512-thread blocks per SM.
+    // blocks per SM); fuller batches on small networks, and batches over several
+    // networks (mostly small ones: the ragged batch of 64 networks took 4.59 ms with
+    // 1,024 threads against 2.71 ms with 512), run two 512-thread blocks per SM.
     // A tuned shape or opts->block overrides.
     p.block = (o && o->block) ? o->block
-              : (tb ? tb : (n >= 1 && (n <= d.sms || vmax >= kWideMinStops) ? 1024 : 512));
+              : (tb ? tb
+                    : (n >= 1 && (n <= d.sms || (n_nets == 1 && vmax >= kWideMinStops)) ? 1024 : 512));
     if (p.block < 64 || p.block > 1024 || p.block % 32)
         return fail(EAT_ERR_INVALID, "block must be a multiple of 32 in 64..1024");
     int vw = (o && o->vwarp) ? o->vwarp : (tv ? tv : 8);
@@ -449,12 +452,14 @@ static int make_plan(int dev, int32_t vmax, int32_t n, int n_nets, const eat_que
         return fail(EAT_ERR_INVALID, "order must be one of EAT_ORDER_*");
     int rc = make_plan_core(dev, vmax, n, n_nets, o, p, vmin < 0 ? vmax : vmin, tuned, own_workspace);
     if (rc) return rc;
-    // Automatic: sorted when some queries must wait for a free block (they then start
-    // longest first) and in the paired mode (an early query shares its block with a
-    // late one); a batch that starts all at once gains nothing for the sort's launch.
+    // Automatic, on one network: sorted when some queries must wait for a free block
+    // (they then start longest first) and in the paired mode (an early query shares its
+    // block with a late one); a batch that starts all at once gains nothing for the
+    // sort's launch.  Batches over several networks keep index order (measured only so).
     const bool waits = p.cluster == 0 && !p.pair && n > p.grid;
     if (own_workspace && n > 1 &&
-        (order == EAT_ORDER_BY_TIME || (order == EAT_ORDER_AUTO && (waits || p.pair)))) {
+        (order == EAT_ORDER_BY_TIME ||
+         (order == EAT_ORDER_AUTO && n_nets == 1 && (waits || p.pair)))) {
         p.order = true;
         p.off_order = align_up(p.ws_bytes, 256);
         p.ws_bytes = p.off_order + align_up((size_t)n * 4, 256);
