@@ -4,7 +4,10 @@ Workload (default "city"): a 20,000-stop random geometric transit network (k = 4
 nearest neighbours, 400 routes of 30-60 stops run both ways, headways 5-20 min,
 20 % jittered trips, peak durations x1.3), about 3.6 M connections; one step =
 one batch of 256 queries (random source with departures, t_s uniform in
-05:00-22:00), all relaxation rounds of all queries in one launch.
+05:00-22:00), all relaxation rounds of all queries in one launch (the launch
+shape by the library's autotuner unless given; batches whose queries cannot all
+start at once begin with the library's sort of the queries by t_s, inside the
+timed region).
 
 Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on the
 launching stream; L2 is flushed (a 256 MB buffer is written) before every step,
@@ -15,8 +18,9 @@ memory (the kernel reads the queries and writes each converged row to host memor
 in place).
 
 Roofline: algorithmic bytes per launch come from the kernel's own per-query work
-counters (stops expanded, types examined, AP records read, relaxations) times the
-fixed per-unit byte figures in BYTES below.
+counters (stops expanded, types examined, AP records read, relaxations), taken in an
+untimed pass over the same batches, times the fixed per-unit byte figures in BYTES
+below.
 
 `--impl reference` times the CPU oracle (connection scan, Algorithm 1) on the host
 cores on the same queries instead.
