@@ -16,6 +16,8 @@ Contents, each following the paper:
   * `cluster_sets`: the partition of a connection type into clusters by
     departure time, cluster k holding departures in [t0 + kW, t0 + (k+1)W)
     (Section III-D with W = 3600 and t0 = 0: departures in [k:00:00, k:59:59]).
+  * `connection_types`: the partition of C into connection types C_{u,v,lambda}
+    (Section III-B), each type's departures sorted and merged.
 """
 from __future__ import annotations
 
