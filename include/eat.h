@@ -172,6 +172,12 @@ typedef struct {
     int32_t cluster;         /* blocks per query in EAT_MODE_CLUSTER: 2, 4 or 8; 0 = 8 */
     int32_t order;           /* EAT_ORDER_*: the order in which a batch's queries start;
                                 0 = automatic */
+    int32_t idle_cap;        /* EAT_MODE_ASYNC only: a warp whose scans of 32 words of
+                                the pending-stop bitmap find nothing this many times in a
+                                row (checked after each full pass) while other warps still
+                                hold work gives up the query, which then reports
+                                EAT_ERR_NO_CONVERGENCE with upper bounds in its row;
+                                0 = 2^24 (far beyond any wait of a correct run) */
     int32_t *status;         /* optional [n] per-query eat_status, device memory */
     eat_counters *counters;  /* optional [n] per-query counters, device memory */
 } eat_query_opts;
@@ -335,7 +341,8 @@ size_t eat_workspace_bytes(const eat_net *const *nets, int32_t n_nets, int32_t n
  * eat_launch_shape -- the launch shape eat_query_batch(_multi) would use for n
  * queries over the given networks with these options (opts may be NULL): *shape
  * receives a copy of *opts with block, vwarp, mode (EAT_MODE_CTA, _CLUSTER,
- * _ASYNC or _PAIR, never _AUTO) and cluster filled in.  Nothing is launched.
+ * _ASYNC or _PAIR, never _AUTO), cluster and order (EAT_ORDER_BY_TIME or
+ * EAT_ORDER_AS_GIVEN, never _AUTO) filled in.  Nothing is launched.
  * Returns EAT_OK, or the error the batch call would report for these options.
  */
 int eat_launch_shape(const eat_net *const *nets, int32_t n_nets, int32_t n,
@@ -427,6 +434,26 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
  */
 int eat_autotune(eat_net *net, const int32_t *sources, const int32_t *times, int32_t n,
                  eat_query_opts *best, void *stream);
+
+/*
+ * eat_autotune_multi -- choose the launch shape and start order of a batch over several
+ * networks of uneven size (eat_query_batch_multi) by measurement; no counterpart in the
+ * paper, as for eat_autotune.  Candidates, in this order: start order as given, then by
+ * t_s (EAT_ORDER_AS_GIVEN, EAT_ORDER_BY_TIME); for each, block sizes 512, 1024 and 256
+ * threads, each with the round-based mode and vwarp 8, 4, 16, 2, 32, then the
+ * asynchronous mode; shapes without a plan for these networks are skipped.  They run on
+ * the sample batch (net_idx, sources, times: [n] int32 device memory; rows packed in
+ * query order in a scratch buffer) and are timed as eat_autotune times them (nine rounds,
+ * cold L2, median, earliest within 5 % wins).  Nothing is stored in the networks: the
+ * caller passes *best (block, vwarp, mode and order filled in, the rest zero) as the
+ * options of its eat_query_batch_multi calls.  Blocks until done; allocates its scratch
+ * for the duration of the call.
+ * Errors: EAT_ERR_INVALID (NULL best, bad networks or indices, host arrays, no shape
+ * fits), EAT_ERR_NO_DEVICE, EAT_ERR_OOM, EAT_ERR_CUDA.
+ */
+int eat_autotune_multi(const eat_net *const *nets, int32_t n_nets, const int32_t *net_idx,
+                       const int32_t *sources, const int32_t *times, int32_t n,
+                       eat_query_opts *best, void *stream);
 
 /* ------------------------------------------------------------------ serving
  * A request loop with continuous batching over resident networks (no

@@ -94,7 +94,8 @@ static int device_info(int dev, DeviceInfo &out) {
         for (int nets : {1, EAT_MAX_NETS})
             for (int mem = 0; mem < 4; ++mem)
                 for (const void *k : {cta_kernel(nets, mem), async_kernel(nets, mem), cluster_kernel(),
-                                      cta_kernel(1, 0, true), pair_kernel(false), pair_kernel(true)}) {
+                                      cta_kernel(1, 0, true), pair_kernel(false), pair_kernel(true),
+                                      ring_kernel(mem)}) {
                     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(d.smem_optin - d.reserve));
                     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
@@ -132,6 +133,7 @@ struct Plan {
 };
 
 static constexpr size_t kWsHeader = 256;   // work counter + internal status / counters
+static constexpr int32_t kDefaultIdleCap = 1 << 24;   // round-free mode's wait limit (full scans)
 static constexpr size_t kQueueEntryBytes = 16;  // (stop, type) item x 2 buffers
 
 // Plan of the round-free kernel: arrivals (shared when they fit), one bitmap and
@@ -498,6 +500,9 @@ static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net
     qa.arr_rows = nullptr;
     qa.arr_rows_stride = 0;
     qa.order = p.order ? (const int32_t *)(ws + p.off_order) : nullptr;
+    qa.spec = 0;
+    qa.idle_cap = kDefaultIdleCap;
+    qa.rg = RingArgs{};
     return qa;
 }
 
@@ -505,6 +510,15 @@ static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net
 // and the output rows are host memory (0 when every query's arrivals are shared).
 static size_t arr_rows_bytes(const Plan &p) {
     return p.mem == 0 ? 0 : (size_t)p.grid * align_up((size_t)p.vmax, 64) * 4;
+}
+
+// Whether the per-query kernel's two-word items can carry the cluster slot of their
+// stop's arrival at push time (type | slot << 24): every network of the launch has
+// fewer than 2^24 connection types and at most 255 cluster slots (slot 255 = none).
+static bool spec_items(const eat_net *const *nets, int n_nets) {
+    for (int i = 0; i < n_nets; ++i)
+        if (nets[i]->host.n_types >= (1 << 24) || nets[i]->host.y > 255) return false;
+    return true;
 }
 
 static int ensure_buffer(void *&buf, size_t &cap, size_t need) {
@@ -545,6 +559,8 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
     QueryArgs qa = make_args(p, p.grid, (char *)ws, net_idx, src, ts, n, n_nets, arr_out, arr_off,
                              cap, status_override ? status_override : (o ? o->status : nullptr),
                              counters_override ? counters_override : (o ? o->counters : nullptr));
+    qa.spec = spec_items(nets, n_nets) ? 1 : 0;
+    if (o && o->idle_cap > 0) qa.idle_cap = o->idle_cap;
     if (arr_rows && p.mem != 0) {
         if (arr_rows_size < arr_rows_bytes(p)) return fail(EAT_ERR_INVALID, "arrival rows too small");
         qa.arr_rows = arr_rows;
@@ -782,6 +798,7 @@ int eat_launch_shape(const eat_net *const *nets, int32_t n_nets, int32_t n,
     shape->mode = p.cluster ? EAT_MODE_CLUSTER : p.pair ? EAT_MODE_PAIR
                   : p.async ? EAT_MODE_ASYNC : EAT_MODE_CTA;
     shape->cluster = p.cluster;
+    shape->order = p.order ? EAT_ORDER_BY_TIME : EAT_ORDER_AS_GIVEN;
     return EAT_OK;
 }
 
@@ -1032,69 +1049,40 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
 
 // ------------------------------------------------------------------ autotuning
 
-extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t *times,
-                            int32_t n, eat_query_opts *best, void *stream) {
-    clear_error();
-    if (!net) return fail(EAT_ERR_INVALID, "NULL network");
-    if (net->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
-    if (n <= 0 || !sources || !times) return fail(EAT_ERR_INVALID, "empty sample");
-    DeviceGuard guard(net->device);
-    if (!is_device_ptr(sources) || !is_device_ptr(times))
-        return fail(EAT_ERR_INVALID, "sample arrays must be device memory");
-    cudaStream_t st = (cudaStream_t)stream;
-    const eat_net *nets[1] = {net};
-    struct Cand {
-        int m, b, v;
-        std::vector<float> ms;
-    };
-    std::vector<Cand> cands;
-    // Fixed order, the library's default shape first (rounds, vwarp 8, 1,024 threads on
-    // networks of 8,192 stops or more, else 512): ties below go to the earliest.
-    DeviceInfo dinfo;
-    int drc = device_info(net->device, dinfo);
-    if (drc) return drc;
-    std::vector<Cand> pairs;
-    if (n > dinfo.sms) {
-        eat_query_opts o{};
-        o.mode = EAT_MODE_PAIR;
-        if (eat_workspace_bytes(nets, 1, n, &o))
-            for (int v : {8, 4, 16}) pairs.push_back({EAT_MODE_PAIR, 1024, v, {}});
-        else clear_error();                  // network too large for two rows per block
-    }
-    const bool wide = net->host.n_stops >= kWideMinStops || n <= dinfo.sms;
-    for (int b : {wide ? 1024 : 512, wide ? 512 : 1024, 256}) {
-        for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, {}});
-        eat_query_opts o{};
-        o.block = b;
-        o.vwarp = 8;
-        o.mode = EAT_MODE_ASYNC;
-        if (eat_workspace_bytes(nets, 1, n, &o)) cands.push_back({EAT_MODE_ASYNC, b, 8, {}});
-        else clear_error();                  // bitmap does not fit: not a candidate
-    }
-    cands.insert(cands.end(), pairs.begin(), pairs.end());
-    size_t ws_need = 0;
-    std::vector<Cand> usable;                // shapes that have a plan on this device
-    for (const Cand &cd : cands) {
-        eat_query_opts o{};
-        o.block = cd.b;
-        o.vwarp = cd.v;
-        o.mode = cd.m;
-        const size_t need = eat_workspace_bytes(nets, 1, n, &o);
-        if (!need) continue;
-        ws_need = std::max(ws_need, need);
-        usable.push_back(cd);
-    }
-    if (usable.empty()) return fail(EAT_ERR_INVALID, "no launch shape fits this network");
-    clear_error();
-    cands.swap(usable);
-    // Every timed run starts with a cold L2: a write of twice the L2 size first.
+namespace eat {
+
+struct TuneCand {
+    int m, b, v, ord;            // mode, block, vwarp, start order (EAT_ORDER_*)
+    std::vector<float> ms;
+};
+
+static eat_query_opts cand_opts(const TuneCand &cd) {
+    eat_query_opts o{};
+    o.block = cd.b;
+    o.vwarp = cd.v;
+    o.mode = cd.m;
+    o.order = cd.ord;
+    return o;
+}
+
+// Times every candidate with run(opts, workspace, rows) on `st` in nine rounds over
+// all candidates (so that slow drift of the clock affects all alike): round 0 warms
+// up, rounds 1..8 are timed with CUDA events, each after a write of twice the L2
+// size so that every timing starts with the networks out of cache.  The earliest
+// candidate whose median is within 5 % of the least median wins (closer differences
+// are within the spread between batches of one workload), so that repeated tuning
+// settles on one shape.  Allocates its scratch (workspace, rows, flush buffer) for
+// the duration of the call.
+template <class Run>
+static int time_candidates(int dev, std::vector<TuneCand> &cands, size_t ws_need, size_t rows_bytes,
+                           cudaStream_t st, const Run &run, TuneCand &best) {
     int l2 = 0;
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, net->device);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     const size_t flush_bytes = std::max<size_t>(2 * (size_t)std::max(l2, 0), 64u << 20);
     void *ws = nullptr, *rows = nullptr, *flush = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc(&ws, ws_need);
-    if (e == cudaSuccess) e = cudaMalloc(&rows, (size_t)n * (size_t)net->host.n_stops * 4);
+    cudaError_t e = cudaMalloc(&ws, std::max<size_t>(ws_need, 256));
+    if (e == cudaSuccess) e = cudaMalloc(&rows, std::max<size_t>(rows_bytes, 256));
     if (e == cudaSuccess) e = cudaMalloc(&flush, flush_bytes);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -1103,15 +1091,9 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
         cudaGetLastError();
         rc = fail(EAT_ERR_OOM, std::string("autotune scratch: ") + cudaGetErrorString(e));
     }
-    // Rounds over all candidates (so that slow drift of the clock affects all
-    // alike): round 0 warms up, rounds 1..kTimed are timed.
     constexpr int kTimed = 8;
     for (int rep = 0; rep <= kTimed && !rc; ++rep) {
-        for (Cand &cd : cands) {
-            eat_query_opts o{};
-            o.block = cd.b;
-            o.vwarp = cd.v;
-            o.mode = cd.m;
+        for (TuneCand &cd : cands) {
             if (rep > 0) {
                 e = cudaMemsetAsync(flush, rep & 0xff, flush_bytes, st);
                 if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -1120,8 +1102,8 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
                     break;
                 }
             }
-            rc = run_batch(nets, 1, nullptr, sources, times, n, (int32_t *)rows, nullptr, ws, ws_need,
-                           &o, st, nullptr, nullptr);
+            const eat_query_opts o = cand_opts(cd);
+            rc = run(o, ws, ws_need, (int32_t *)rows);
             if (rc) break;
             if (rep > 0) {
                 float ms = 0.f;
@@ -1136,41 +1118,171 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
             }
         }
     }
-    // Least median time; shapes within 5 % of it count as tied (the spread of one
-    // shape's time over batches of the same workload), and a tie goes to the earliest
-    // candidate in the fixed order above, so that repeated tuning settles on one shape.
-    float least = 1e30f;
-    for (Cand &cd : cands) {
-        if (cd.ms.size() != (size_t)kTimed) continue;
-        std::sort(cd.ms.begin(), cd.ms.end());
-        cd.ms[0] = 0.5f * (cd.ms[kTimed / 2 - 1] + cd.ms[kTimed / 2]);   // median
-        least = std::min(least, cd.ms[0]);
-    }
-    int best_b = 512, best_v = 8, best_m = EAT_MODE_CTA;
-    for (const Cand &cd : cands) {
-        if (cd.ms.size() == (size_t)kTimed && cd.ms[0] <= least * 1.05f) {
-            best_b = cd.b;
-            best_v = cd.v;
-            best_m = cd.m;
-            break;
-        }
-    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (ws) cudaFree(ws);
     if (rows) cudaFree(rows);
     if (flush) cudaFree(flush);
     if (rc) return rc;
+    float least = 1e30f;
+    for (TuneCand &cd : cands) {
+        if (cd.ms.size() != (size_t)kTimed) continue;
+        std::sort(cd.ms.begin(), cd.ms.end());
+        cd.ms[0] = 0.5f * (cd.ms[kTimed / 2 - 1] + cd.ms[kTimed / 2]);   // median
+        least = std::min(least, cd.ms[0]);
+    }
+    for (const TuneCand &cd : cands) {
+        if (cd.ms.size() == (size_t)kTimed && cd.ms[0] <= least * 1.05f) {
+            best = cd;
+            return EAT_OK;
+        }
+    }
+    return fail(EAT_ERR_INVALID, "no candidate was timed");
+}
+
+// Keeps the candidates that have a plan for these networks; ws_need = the largest
+// workspace among them.
+static int usable_candidates(const eat_net *const *nets, int n_nets, int32_t n,
+                             std::vector<TuneCand> &cands, size_t &ws_need) {
+    ws_need = 0;
+    std::vector<TuneCand> usable;
+    for (const TuneCand &cd : cands) {
+        const eat_query_opts o = cand_opts(cd);
+        const size_t need = eat_workspace_bytes(nets, n_nets, n, &o);
+        if (!need) continue;
+        ws_need = std::max(ws_need, need);
+        usable.push_back(cd);
+    }
+    clear_error();
+    if (usable.empty()) return fail(EAT_ERR_INVALID, "no launch shape fits these networks");
+    cands.swap(usable);
+    return EAT_OK;
+}
+
+}  // namespace eat
+
+extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t *times,
+                            int32_t n, eat_query_opts *best, void *stream) {
+    clear_error();
+    if (!net) return fail(EAT_ERR_INVALID, "NULL network");
+    if (net->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
+    if (n <= 0 || !sources || !times) return fail(EAT_ERR_INVALID, "empty sample");
+    DeviceGuard guard(net->device);
+    if (!is_device_ptr(sources) || !is_device_ptr(times))
+        return fail(EAT_ERR_INVALID, "sample arrays must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    const eat_net *nets[1] = {net};
+    std::vector<TuneCand> cands;
+    // Fixed order, the library's default shape first (rounds, vwarp 8, 1,024 threads on
+    // networks of 8,192 stops or more, else 512): ties go to the earliest.
+    DeviceInfo dinfo;
+    int drc = device_info(net->device, dinfo);
+    if (drc) return drc;
+    std::vector<TuneCand> pairs;
+    if (n > dinfo.sms) {
+        eat_query_opts o{};
+        o.mode = EAT_MODE_PAIR;
+        if (eat_workspace_bytes(nets, 1, n, &o))
+            for (int v : {8, 4, 16}) pairs.push_back({EAT_MODE_PAIR, 1024, v, EAT_ORDER_AUTO, {}});
+        else clear_error();                  // network too large for two rows per block
+    }
+    const bool wide = net->host.n_stops >= kWideMinStops || n <= dinfo.sms;
+    for (int b : {wide ? 1024 : 512, wide ? 512 : 1024, 256}) {
+        for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, EAT_ORDER_AUTO, {}});
+        cands.push_back({EAT_MODE_ASYNC, b, 8, EAT_ORDER_AUTO, {}});
+    }
+    cands.insert(cands.end(), pairs.begin(), pairs.end());
+    size_t ws_need = 0;
+    int rc = usable_candidates(nets, 1, n, cands, ws_need);
+    if (rc) return rc;
+    TuneCand win{EAT_MODE_CTA, 512, 8, EAT_ORDER_AUTO, {}};
+    rc = time_candidates(net->device, cands, ws_need, (size_t)n * (size_t)net->host.n_stops * 4, st,
+                         [&](const eat_query_opts &o, void *ws, size_t wsb, int32_t *rows) {
+                             return run_batch(nets, 1, nullptr, sources, times, n, rows, nullptr,
+                                              ws, wsb, &o, st, nullptr, nullptr);
+                         },
+                         win);
+    if (rc) return rc;
     int cls = 0;
     while (cls < 31 && (1 << (cls + 1)) <= n) ++cls;
-    net->tuned[cls].store((uint32_t)best_b | (uint32_t)best_v << 16 | (uint32_t)best_m << 24,
+    net->tuned[cls].store((uint32_t)win.b | (uint32_t)win.v << 16 | (uint32_t)win.m << 24,
                           std::memory_order_relaxed);
     if (best) {
         *best = eat_query_opts{};
-        best->block = best_b;
-        best->vwarp = best_v;
-        best->mode = best_m;
+        best->block = win.b;
+        best->vwarp = win.v;
+        best->mode = win.m;
     }
+    return EAT_OK;
+}
+
+extern "C" int eat_autotune_multi(const eat_net *const *nets, int32_t n_nets, const int32_t *net_idx,
+                                  const int32_t *sources, const int32_t *times, int32_t n,
+                                  eat_query_opts *best, void *stream) {
+    clear_error();
+    if (!best) return fail(EAT_ERR_INVALID, "best must not be NULL");
+    if (!nets || n_nets < 1 || n_nets > EAT_MAX_NETS) return fail(EAT_ERR_INVALID, "bad nets");
+    for (int i = 0; i < n_nets; ++i) {
+        if (!nets[i]) return fail(EAT_ERR_INVALID, "NULL network");
+        if (nets[i]->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
+        if (nets[i]->device != nets[0]->device)
+            return fail(EAT_ERR_INVALID, "all networks must be on one device");
+    }
+    if (n <= 0 || !net_idx || !sources || !times) return fail(EAT_ERR_INVALID, "empty sample");
+    const int dev = nets[0]->device;
+    DeviceGuard guard(dev);
+    if (!is_device_ptr(net_idx) || !is_device_ptr(sources) || !is_device_ptr(times))
+        return fail(EAT_ERR_INVALID, "sample arrays must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    // Output rows packed in query order: offsets from the sample's network indices.
+    std::vector<int32_t> idx((size_t)n);
+    cudaError_t e = cudaMemcpy(idx.data(), net_idx, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy of the sample's network indices");
+    std::vector<int64_t> offs((size_t)n);
+    int64_t total = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (idx[i] < 0 || idx[i] >= n_nets) return fail(EAT_ERR_INVALID, "net_idx out of range");
+        offs[i] = total;
+        total += nets[idx[i]]->host.n_stops;
+    }
+    int64_t *d_offs = nullptr;
+    e = cudaMalloc(&d_offs, (size_t)n * 8);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EAT_ERR_OOM, "autotune scratch (row offsets)");
+    }
+    e = cudaMemcpy(d_offs, offs.data(), (size_t)n * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_offs);
+        return cuda_fail(e, "cudaMemcpy of the row offsets");
+    }
+    // Candidates in a fixed order, the library's default for a batch over several
+    // networks first (512 threads, vwarp 8, index order): block sizes 512, 1,024 and
+    // 256, each with vwarp 8, 4, 16, 2, 32 and the round-free mode, each in index
+    // order and then in order of t_s.
+    std::vector<TuneCand> cands;
+    for (int ord : {EAT_ORDER_AS_GIVEN, EAT_ORDER_BY_TIME})
+        for (int b : {512, 1024, 256}) {
+            for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, ord, {}});
+            cands.push_back({EAT_MODE_ASYNC, b, 8, ord, {}});
+        }
+    size_t ws_need = 0;
+    int rc = usable_candidates(nets, n_nets, n, cands, ws_need);
+    TuneCand win{EAT_MODE_CTA, 512, 8, EAT_ORDER_AS_GIVEN, {}};
+    if (!rc)
+        rc = time_candidates(dev, cands, ws_need, (size_t)total * 4, st,
+                             [&](const eat_query_opts &o, void *ws, size_t wsb, int32_t *rows) {
+                                 return run_batch(nets, n_nets, net_idx, sources, times, n, rows,
+                                                  d_offs, ws, wsb, &o, st, nullptr, nullptr);
+                             },
+                             win);
+    cudaFree(d_offs);
+    if (rc) return rc;
+    *best = eat_query_opts{};
+    best->block = win.b;
+    best->vwarp = win.v;
+    best->mode = win.m;
+    best->order = win.ord;
     return EAT_OK;
 }
 
@@ -1235,6 +1347,8 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     QueryArgs qa = make_args(p, grid, (char *)scratch, nullptr, sources, times, n, 1, arr_out,
                              nullptr, cap, opts ? opts->status : nullptr,
                              opts ? opts->counters : nullptr);
+    qa.spec = spec_items(&net, 1) ? 1 : 0;
+    if (opts && opts->idle_cap > 0) qa.idle_cap = opts->idle_cap;
     cudaStream_t st = (cudaStream_t)stream;
     // The query counter must start at zero; the queues need no clearing.
     cudaError_t e = cudaMemsetAsync(qa.work, 0, sizeof(int32_t), st);

@@ -60,18 +60,67 @@ __device__ __forceinline__ int32_t next_query(const QueryArgs &qa) {
     return (qa.order && w < qa.n) ? __ldg(qa.order + w) : w;
 }
 
+// Ring mode: thread 0 of a block claims the next published request (a CAS on the
+// device-side head below the host's tail, read with acquire semantics so that the
+// entry written before it is visible), copies its fields to s_ring and returns its
+// ring slot; it returns -1 when the host's stop flag is set and nothing is left, or
+// after rg.idle_iters polls without a request (every wait bounded).
+__device__ __forceinline__ int64_t ld_acquire_sys(const int64_t *p) {
+    int64_t v;
+    asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ int32_t ring_next(const RingArgs &R, int32_t *s_ring) {
+    for (int32_t it = 0; it < R.idle_iters; ++it) {
+        const int64_t tail = ld_acquire_sys(R.tail);
+        unsigned long long h = *(volatile unsigned long long *)R.head;
+        while ((int64_t)h < tail) {
+            const unsigned long long was = atomicCAS(R.head, h, h + 1);
+            if (was == h) {
+                const int32_t slot = (int32_t)(h & (unsigned long long)R.mask);
+                const volatile RingEntry *e = R.ring + slot;
+                s_ring[0] = e->net;
+                s_ring[1] = e->src;
+                s_ring[2] = e->ts;
+                s_ring[3] = e->row;
+                return slot;
+            }
+            h = was;
+        }
+        if (*(const volatile int32_t *)R.stop) return -1;
+        __nanosleep(2000);
+    }
+    return -1;
+}
+
+// Ring mode: publish request `slot` as finished (its row is already written by the
+// block, ordered before this by the block barrier and the release).
+__device__ __forceinline__ void ring_done(const RingArgs &R, int32_t slot, int32_t status) {
+    RingEntry *e = R.ring + slot;
+    *(volatile int32_t *)&e->status = status;
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(&e->done), "r"(1) : "memory");
+}
+
 constexpr int32_t kNullItem = -1;           // hole left by a stop that spilled
 constexpr int32_t kFirstItem = INT32_MIN;    // flag on the first item of a stop
+constexpr int32_t kNoSlot = 255;             // item tag: no cluster slot recorded
+
+// Cluster entry of type t for stored cluster slot k (cluster-major table).
+__device__ __forceinline__ const int4 *entry_at(const NetDev &N, int32_t k, int32_t t) {
+    return N.ce + 2 * ((int64_t)k * N.n_types + t);
+}
 
 // Items are (stop, type) pairs in two int32 arrays per buffer, or, with PACK (networks
 // of at most 32,767 stops and 65,535 types), one word per item: first-item flag << 31 |
 // stop << 16 | type, which doubles the items a buffer holds in the same shared memory
 // (kNullItem is then no valid item: it would be stop 32,767, type 65,535).
-template <int NETS, int ARR, bool SMEM_MASK, bool PACK = false>
+template <int NETS, int ARR, bool SMEM_MASK, bool PACK = false, bool RING = false>
 __global__ void __launch_bounds__(1024, 1)
 eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) {
     extern __shared__ __align__(16) int32_t smem[];
     __shared__ int32_t s_q;
+    __shared__ int32_t s_ring[4];     // ring mode: net, source, t_s, row of the request
     __shared__ int32_t s_items[3];    // items reserved per round (rotating)
     __shared__ int32_t s_spill[3];    // stops spilled per round (rotating)
     __shared__ unsigned long long s_cnt[6];
@@ -91,17 +140,19 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                                           : qa.gmask + (int64_t)blockIdx.x * qa.mask_stride;
 
     for (;;) {
-        if (tid == 0) s_q = next_query(qa);
+        if (tid == 0) s_q = RING ? ring_next(qa.rg, s_ring) : next_query(qa);
         if (tid < 6) s_cnt[tid] = 0;
         __syncthreads();
         const int q = s_q;
-        if (q >= qa.n) break;
+        if (RING ? q < 0 : q >= qa.n) break;
 
-        const int ni = qa.net_idx == nullptr ? 0 : __ldg(qa.net_idx + q);
+        const int ni = RING ? s_ring[0] : qa.net_idx == nullptr ? 0 : __ldg(qa.net_idx + q);
         const bool net_ok = (unsigned)ni < (unsigned)qa.n_nets;
         const NetDev &N = nets.net[net_ok ? ni : 0];
         const int32_t V = N.n_stops;
-        const int64_t off = qa.arr_off ? __ldg(qa.arr_off + q) : (int64_t)q * V;
+        const int64_t off = RING         ? (int64_t)s_ring[3] * qa.rg.row_stride
+                            : qa.arr_off ? __ldg(qa.arr_off + q)
+                                         : (int64_t)q * V;
         int32_t *const out = qa.arr_out + off;
         const bool arr_shared = ARR == kArrShared || (ARR == kArrPerQuery && V <= qa.smem_arr_cap);
         // Arrivals: shared memory, else the block's scratch row (when the output is
@@ -123,8 +174,8 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             s_items[tid] = 0;
             s_spill[tid] = 0;
         }
-        const int32_t s = __ldg(qa.src + q);
-        const int32_t t_s = __ldg(qa.ts + q);
+        const int32_t s = RING ? s_ring[1] : __ldg(qa.src + q);
+        const int32_t t_s = RING ? s_ring[2] : __ldg(qa.ts + q);
         const bool valid = net_ok && (unsigned)s < (unsigned)V;
         __syncthreads();
         // The source is the frontier of "round -1": spill queue of buffer 1, counter slot 2.
@@ -156,15 +207,17 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                 s_spill[nx] = 0;
             }
 
-            // Relax type t of tail u (Algorithm 3 with getConnection, Algorithm 6);
-            // on success v joins the next frontier as items or as a spilled stop.
-            auto relax = [&](int32_t e_u, int32_t k, int32_t t) {
+            // Relax one type of tail u from its cluster entry (Algorithm 3 with
+            // getConnection, Algorithm 6); when t_c + lambda is below the e[v] read just
+            // before, lower e[v] with an atomic min whose result is not waited for and put
+            // v on the next frontier as items or as a spilled stop.  Every lowering is
+            // made by a thread whose candidate was below its read, so every lowering
+            // pushes v (at most once a round: the bitmap); a push whose min lost to a
+            // lower one made meanwhile only repeats work.
+            auto relax_entry = [&](int32_t e_u, int32_t k, const int4 ca, const int4 cb) {
                 ++c_types;
                 ++c_lookups;
-                const int4 *c = N.ce + 2 * ((int64_t)k * N.n_types + t);
-                int4 ca, cb;                                // cb = {x|n, v, lambda|d, row of v}
-                load_entry(c, ca, cb);
-                int32_t n, x;
+                int32_t n, x;                               // cb = {x|n, v, lambda|d, row of v}
                 entry_aps(cb, N.apx, n, x);
                 const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, k), e_u, N.apx, c_aps);
                 if (tc == kInf) return;                     // no departure left (Section IV-D)
@@ -172,8 +225,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                 const int32_t v = cb.y;
                 const int32_t cand = tc + (cb.z & 0xffffff);
                 if (cand >= load_arr(arr, v, arr_shared)) return;
-                const int32_t old = atomicMin(arr + v, cand);
-                if (cand >= old) return;
+                atomicMin(arr + v, cand);
                 ++c_relax;
                 int32_t d = (int32_t)((uint32_t)cb.z >> 24);  // types leaving v
                 if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - cb.w;
@@ -188,11 +240,17 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                         iu_wr[base] = hv | kFirstItem;
                         for (int32_t j = 1; j < d; ++j) iu_wr[base + j] = hv + j;
                     } else {
+                        // The cluster slot of v's arrival now, for next round's entry load.
+                        int32_t tag = 0;
+                        if (qa.spec) {
+                            const int32_t kv = cluster_slot(N, cand);
+                            tag = (int32_t)((uint32_t)(kv < N.y ? kv : kNoSlot) << 24);
+                        }
                         iu_wr[base] = v | kFirstItem;
-                        it_wr[base] = ty.z;
+                        it_wr[base] = ty.z | tag;
                         for (int32_t j = 1; j < d; ++j) {
                             iu_wr[base + j] = v;
-                            it_wr[base + j] = ty.z + j;
+                            it_wr[base + j] = (ty.z + j) | tag;
                         }
                     }
                 } else {
@@ -201,7 +259,9 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                 }
             };
 
-            // One thread per (stop, type) item.
+            // One thread per (stop, type) item.  Two-word items tagged with a cluster
+            // slot load that slot's entry at once, beside e[u], and load again only
+            // when e[u] has since moved to another cluster.
             for (int32_t i = tid; i < n_items; i += nthr) {
                 const int32_t raw = iu_rd[i];
                 if (raw == kNullItem) continue;
@@ -210,13 +270,24 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                     atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
                     ++c_vert;
                 }
+                int32_t t, ks = kNoSlot;
+                if (PACK) {
+                    t = raw & 0xffff;
+                } else {
+                    const int32_t w = it_rd[i];
+                    t = qa.spec ? w & 0xffffff : w;
+                    if (qa.spec) ks = (int32_t)((uint32_t)w >> 24);
+                }
+                int4 ca, cb;
+                if (!PACK && ks != kNoSlot) load_entry(entry_at(N, ks, t), ca, cb);
                 const int32_t e_u = load_arr(arr, u, arr_shared);
                 const int32_t k = cluster_slot(N, e_u);
                 if (k >= N.y) {                             // no departure left anywhere
                     ++c_types;
                     continue;
                 }
-                relax(e_u, k, PACK ? raw & 0xffff : it_rd[i]);
+                if (PACK || k != ks) load_entry(entry_at(N, k, t), ca, cb);
+                relax_entry(e_u, k, ca, cb);
             }
             // Spilled stops: `vw` lanes per stop stride over its types.
             for (int32_t i = sub; i < n_spill; i += nsub) {
@@ -233,7 +304,11 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                     if (lane == 0) c_types += end - beg;
                     continue;
                 }
-                for (int32_t t = beg + lane; t < end; t += vw) relax(e_u, k, t);
+                for (int32_t t = beg + lane; t < end; t += vw) {
+                    int4 ca, cb;
+                    load_entry(entry_at(N, k, t), ca, cb);
+                    relax_entry(e_u, k, ca, cb);
+                }
             }
             __syncthreads();
             n_items = min(s_items[cs], icap);
@@ -247,9 +322,14 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             __syncthreads();
             for (int32_t i = tid; i < V; i += nthr) out[i] = load_arr(arr, i, arr_shared);
         }
-        if (tid == 0 && qa.status)
-            qa.status[q] = !valid ? EAT_ERR_INVALID : (F > 0 ? EAT_ERR_NO_CONVERGENCE : EAT_OK);
-        if (qa.counters) {
+        const int32_t q_status = !valid ? EAT_ERR_INVALID : (F > 0 ? EAT_ERR_NO_CONVERGENCE : EAT_OK);
+        if (RING) {
+            __syncthreads();                              // the whole row is written
+            if (tid == 0) ring_done(qa.rg, q, q_status);
+        } else if (tid == 0 && qa.status) {
+            qa.status[q] = q_status;
+        }
+        if (!RING && qa.counters) {
             unsigned long long c[6] = {(unsigned long long)c_vert, (unsigned long long)c_types,
                                        (unsigned long long)c_evals, (unsigned long long)c_lookups,
                                        (unsigned long long)c_aps, (unsigned long long)c_relax};
@@ -468,8 +548,7 @@ eat_pair_kernel(const __grid_constant__ NetTable<1> nets, const QueryArgs qa) {
             const int32_t v = cb.y;
             const int32_t cand = tc + (cb.z & 0xffffff);
             if (cand >= load_arr(a, v, true)) return;
-            const int32_t old = atomicMin(a + v, cand);
-            if (cand >= old) return;
+            atomicMin(a + v, cand);                        // result not waited for, as above
             if (COUNT) pc.add(j, 5, 1);
             int32_t d = (int32_t)((uint32_t)cb.z >> 24);
             if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - cb.w;
@@ -557,9 +636,10 @@ eat_pair_kernel(const __grid_constant__ NetTable<1> nets, const QueryArgs qa) {
 // without the round barrier).  A work counter holds pending + claimed stops:
 // a producer adds one before publishing a bit, a claimed stop is subtracted only
 // after all its pushes, so the counter reaches zero exactly when no work is left.
-// Every idle wait is capped; hitting the cap reports EAT_ERR_NO_CONVERGENCE.
-
-constexpr int32_t kIdleCap = 1 << 24;       // empty chunk scans in a row before giving up
+// Every idle wait is capped (qa.idle_cap scans of 32 bitmap words in a row by one warp
+// that find nothing while work is still counted, checked after each full pass); hitting
+// the cap ends the query with EAT_ERR_NO_CONVERGENCE and the arrivals reached so far
+// (upper bounds).
 
 template <int NETS, int ARR>
 __global__ void __launch_bounds__(1024, 1)
@@ -621,7 +701,7 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
 
         int32_t c_vert = 0, c_types = 0, c_evals = 0, c_lookups = 0, c_aps = 0, c_relax = 0;
         int32_t chunk = nchunks > 0 ? warp % nchunks : 0;
-        int32_t idle = 0, passes = 0;
+        int32_t idle = 0, passes = 0;             // passes: empty chunk scans in a row
         bool go = valid;
         while (go) {
             // Claim up to one pending stop per lane from this chunk's 32 words.
@@ -637,14 +717,14 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
             const uint32_t claimed = __ballot_sync(0xffffffffu, u >= 0);
             if (claimed == 0) {
                 chunk = chunk + 1 == nchunks ? 0 : chunk + 1;
-                ++passes;                         // empty chunk scans in a row
+                ++passes;
                 if (++idle >= nchunks) {          // a full pass found nothing
                     idle = 0;
                     int32_t stop = 0;
                     if (lane == 0) {
                         const int32_t wk = *((volatile int32_t *)&s_work);
                         const int32_t er = *((volatile int32_t *)&s_err);
-                        stop = (wk == 0 || er) ? 1 : (passes > kIdleCap ? 2 : 0);
+                        stop = (wk == 0 || er) ? 1 : (passes >= qa.idle_cap ? 2 : 0);
                         if (stop == 2) atomicExch(&s_err, 1);
                     }
                     stop = __shfl_sync(0xffffffffu, stop, 0);
@@ -1108,6 +1188,27 @@ cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int 
     }
     if (n_nets == 1) return launch_cta_t<1>(nets, n_nets, qa, mem, grid, block, smem, st);
     return launch_cta_t<EAT_MAX_NETS>(nets, n_nets, qa, mem, grid, block, smem, st);
+}
+
+const void *ring_kernel(int mem) {
+    switch (mem) {
+    case 0: return (const void *)eat_cta_kernel<EAT_MAX_NETS, kArrShared, true, false, true>;
+    case 3: return (const void *)eat_cta_kernel<EAT_MAX_NETS, kArrPerQuery, true, false, true>;
+    default: return (const void *)eat_cta_kernel<EAT_MAX_NETS, kArrGlobal, true, false, true>;
+    }
+}
+
+cudaError_t launch_ring(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
+                        int block, size_t smem, cudaStream_t st) {
+    NetTable<EAT_MAX_NETS> tab;
+    for (int i = 0; i < n_nets && i < EAT_MAX_NETS; ++i) tab.net[i] = nets[i];
+    for (int i = n_nets; i < EAT_MAX_NETS; ++i) tab.net[i] = NetDev{};
+    switch (mem) {
+    case 0: eat_cta_kernel<EAT_MAX_NETS, kArrShared, true, false, true><<<grid, block, smem, st>>>(tab, qa); break;
+    case 3: eat_cta_kernel<EAT_MAX_NETS, kArrPerQuery, true, false, true><<<grid, block, smem, st>>>(tab, qa); break;
+    default: eat_cta_kernel<EAT_MAX_NETS, kArrGlobal, true, false, true><<<grid, block, smem, st>>>(tab, qa); break;
+    }
+    return cudaGetLastError();
 }
 
 const void *pair_kernel(bool count) {

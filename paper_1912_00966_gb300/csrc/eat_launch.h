@@ -7,6 +7,28 @@
 
 namespace eat {
 
+// One request of the serving ring (page-locked host memory that the GPU reads and
+// writes in place): the host dispatcher fills net, src, ts, row and clears done before
+// it publishes the ring's tail; the block that ran the request writes the result row,
+// then status, then done = 1 (a system-scope release).
+struct RingEntry {
+    int32_t net, src, ts, row;   // network index, source, departure, result row slot
+    int32_t status;              // eat_status of the request
+    int32_t done;                // 1 once the row and the status are in place
+    int64_t seq;                 // ring position of the request (host bookkeeping)
+};
+
+// Ring-mode arguments: persistent blocks claim requests [head, tail) one at a time.
+struct RingArgs {
+    RingEntry *ring;             // [mask + 1] entries (device address of host memory)
+    const int64_t *tail;         // requests published by the host (host memory)
+    const int32_t *stop;         // nonzero: a block that finds no request leaves (host memory)
+    unsigned long long *head;    // requests claimed so far (device memory, CAS)
+    int64_t row_stride;          // ints per result row of the pool at arr_out
+    int32_t mask;                // ring capacity - 1 (a power of two)
+    int32_t idle_iters;          // polls (about 2 us apart) before an idle block leaves
+};
+
 struct QueryArgs {
     const int32_t *net_idx;    // [n] or nullptr (single network)
     const int32_t *src;        // [n]
@@ -34,6 +56,11 @@ struct QueryArgs {
                                // in shared memory and arr_out is host memory, or nullptr
     int64_t arr_rows_stride;   // ints per block row
     const int32_t *order;      // [n]: the i-th query handed out is order[i], or nullptr (i)
+    int32_t idle_cap;          // round-free mode: empty 32-word bitmap scans in a row per warp
+    int32_t spec;              // two-word items carry the cluster slot of the head's arrival
+                               // at push time (type | slot << 24): every network of the
+                               // launch has < 2^24 types and <= 255 cluster slots
+    RingArgs rg;               // ring mode only
 };
 
 // mem: 0 = arrivals and bitmaps in shared memory, 1 = arrivals global / bitmaps
@@ -44,6 +71,13 @@ struct QueryArgs {
 const void *cta_kernel(int nets, int mem, bool pack = false);
 cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
                        int block, size_t smem, cudaStream_t st, bool pack = false);
+// Ring mode of the per-query kernel (serving): persistent blocks take requests from
+// qa.rg until the host's stop flag is set and no request is left, or until they find
+// none for rg.idle_iters polls; mem 0, 1 or 3; rows go to arr_out + row * row_stride,
+// arrivals not in shared memory live in the block's arr_rows row meanwhile.
+const void *ring_kernel(int mem);
+cudaError_t launch_ring(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
+                        int block, size_t smem, cudaStream_t st);
 // Asynchronous (round-free) kernel; mem 0, 1 or 3 as above (bitmap always shared).
 const void *async_kernel(int nets, int mem);
 cudaError_t launch_async(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,

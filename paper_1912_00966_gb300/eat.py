@@ -83,7 +83,8 @@ class eat_query_opts(ctypes.Structure):
     _fields_ = [("max_rounds", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("vwarp", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("placement", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("order", ctypes.c_int32), ("status", _vp), ("counters", _vp)]
+                ("order", ctypes.c_int32), ("idle_cap", ctypes.c_int32), ("status", _vp),
+                ("counters", _vp)]
 
 
 class eat_server_opts(ctypes.Structure):
@@ -134,6 +135,8 @@ _sig("eat_query_batch_noalloc", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _v
                                                ctypes.POINTER(eat_query_opts), _vp])
 
 _sig("eat_autotune", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.POINTER(eat_query_opts), _vp])
+_sig("eat_autotune_multi", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, _vp, _vp, _vp,
+                                          ctypes.c_int32, ctypes.POINTER(eat_query_opts), _vp])
 _sig("eat_server_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32,
                                          ctypes.POINTER(eat_server_opts), ctypes.POINTER(_vp)])
 _sig("eat_server_submit", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
@@ -163,7 +166,7 @@ _sig("eat_ladder_query", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, cty
                                         ctypes.POINTER(eat_ladder_stats)])
 _sig("eat_ladder_host_view", ctypes.c_int, [_vp, ctypes.POINTER(eat_ladder_view)])
 
-EXPORTED = ("eat_autotune", "eat_server_create", "eat_server_submit", "eat_server_poll", "eat_server_get_stats",
+EXPORTED = ("eat_autotune", "eat_autotune_multi", "eat_server_create", "eat_server_submit", "eat_server_poll", "eat_server_get_stats",
             "eat_server_destroy", "eat_last_error", "eat_version", "eat_build", "eat_build_csr", "eat_free", "eat_get_stats",
             "eat_net_host_view", "eat_query", "eat_workspace_bytes", "eat_launch_shape", "eat_query_batch",
             "eat_query_batch_multi", "eat_next_departure", "eat_query_batch_noalloc",
@@ -308,10 +311,10 @@ def eat_net_host_view(net: Net) -> dict:
     }
 
 
-def _opts(max_rounds=0, block=0, vwarp=0, mode=0, placement=0, cluster=0, order=0, status=None,
-          counters=None):
+def _opts(max_rounds=0, block=0, vwarp=0, mode=0, placement=0, cluster=0, order=0, idle_cap=0,
+          status=None, counters=None):
     return eat_query_opts(int(max_rounds), int(block), int(vwarp), int(mode), int(placement),
-                          int(cluster), int(order), _ptr(status), _ptr(counters))
+                          int(cluster), int(order), int(idle_cap), _ptr(status), _ptr(counters))
 
 
 def eat_query(net: Net, s: int, t_s: int, out=None, counters: bool = False):
@@ -335,7 +338,7 @@ def eat_workspace_bytes(nets, n, **opts) -> int:
 
 
 def eat_launch_shape(nets, n, **opts) -> dict:
-    """Launch shape a batch of n queries would run with: block, vwarp, mode, cluster."""
+    """Launch shape a batch of n queries would run with: block, vwarp, mode, cluster, order."""
     if isinstance(nets, Net):
         nets = [nets]
     arr = (_vp * len(nets))(*[x.handle.value for x in nets])
@@ -343,7 +346,8 @@ def eat_launch_shape(nets, n, **opts) -> dict:
     shape = eat_query_opts()
     _check(_lib.eat_launch_shape(arr, len(nets), int(n), ctypes.byref(o), ctypes.byref(shape)),
            "eat_launch_shape")
-    return {"block": shape.block, "vwarp": shape.vwarp, "mode": shape.mode, "cluster": shape.cluster}
+    return {"block": shape.block, "vwarp": shape.vwarp, "mode": shape.mode, "cluster": shape.cluster,
+            "order": shape.order}
 
 
 def eat_query_batch(net: Net, sources, times, out, workspace=None, workspace_bytes=None,
@@ -393,6 +397,18 @@ def eat_autotune(net: Net, sources, times, stream=None) -> dict:
     _check(_lib.eat_autotune(net.handle, _ptr(sources), _ptr(times), int(sources.shape[0]),
                              ctypes.byref(o), _stream_handle(stream)), "eat_autotune")
     return {"block": o.block, "vwarp": o.vwarp, "mode": o.mode}
+
+
+def eat_autotune_multi(nets, net_idx, sources, times, stream=None) -> dict:
+    """Time the candidate launch shapes and start orders of a batch over several networks
+    (device int32 arrays); returns {"block", "vwarp", "mode", "order"} to pass as the
+    options of eat_query_batch_multi."""
+    arr = (_vp * len(nets))(*[x.handle.value for x in nets])
+    o = eat_query_opts()
+    _check(_lib.eat_autotune_multi(arr, len(nets), _ptr(net_idx), _ptr(sources), _ptr(times),
+                                   int(sources.shape[0]), ctypes.byref(o), _stream_handle(stream)),
+           "eat_autotune_multi")
+    return {"block": o.block, "vwarp": o.vwarp, "mode": o.mode, "order": o.order}
 
 
 def eat_next_departure(net: Net, types, times, out, stream=None):

@@ -13,8 +13,25 @@ def _bench(*args):
                           capture_output=True, text=True, timeout=600, cwd=ROOT)
 
 
+def _line(*args):
+    r = _bench("--impl", "reference", *args)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    return json.loads(lines[0])
+
+
+def test_reference_arm_default_is_the_large_network_sampled():
+    """The default workload is the 200,000-stop network with 1,024 queries per step; the
+    oracle runs a bounded sample of each step's batch, and the line says so."""
+    d = _line("--steps", "1", "--warmup", "3")
+    assert d["config"]["global_batch"] == 1024 and d["config"]["n_stops"] == 200000
+    assert "first 64 queries of each 1,024-query step" in d["cpu_baseline"]["sample"]
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"]
+
+
 def test_reference_arm_line():
-    r = _bench("--impl", "reference", "--steps", "1", "--warmup", "3")
+    r = _bench("--impl", "reference", "--workload", "city", "--steps", "1", "--warmup", "3")
     assert r.returncode == 0, r.stderr
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1

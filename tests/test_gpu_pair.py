@@ -159,17 +159,20 @@ def test_launch_shape_defaults(eat, small, city):
     per SM and on networks of 8,192 stops or more, two 512-thread blocks per SM for larger
     batches on small networks; the paired mode only when asked for (or tuned)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert eat.eat_launch_shape(city.net, sms + 1) == {"block": 1024, "vwarp": 8, "mode": 1, "cluster": 0}
+    assert eat.eat_launch_shape(city.net, sms + 1) == {"block": 1024, "vwarp": 8, "mode": 1, "cluster": 0,
+                                                       "order": eat.EAT_ORDER_BY_TIME}
     assert eat.eat_launch_shape(small.net, sms + 1)["block"] == 512
     assert eat.eat_launch_shape(small.net, sms + 1, mode=PAIR)["mode"] == PAIR
     assert eat.eat_launch_shape(city.net, sms + 1, mode=PAIR)["block"] == 1024
     for case in (small, city):
-        assert eat.eat_launch_shape(case.net, sms) == {"block": 1024, "vwarp": 8, "mode": 1, "cluster": 0}
+        assert eat.eat_launch_shape(case.net, sms) == {"block": 1024, "vwarp": 8, "mode": 1, "cluster": 0,
+                                                       "order": eat.EAT_ORDER_AS_GIVEN}
         assert eat.eat_launch_shape(case.net, 4 * sms, block=512)["mode"] == 1
         assert eat.eat_launch_shape(case.net, 4 * sms, mode=3)["mode"] == 3
     other = eat.eat_build(small.tt.n_stops, small.tt.u, small.tt.v, small.tt.dep, small.tt.dur,
                           device=0)
     assert eat.eat_launch_shape([small.net, other], 4 * sms)["mode"] == 1
+    assert eat.eat_launch_shape([small.net, other], 4 * sms)["order"] == eat.EAT_ORDER_AS_GIVEN
     big = synth.tiny_random(40000, 500, 99)
     net = eat.eat_build(big.n_stops, big.u, big.v, big.dep, big.dur, device=0)
     assert eat.eat_launch_shape(net, 4 * sms)["mode"] == 1

@@ -303,19 +303,62 @@ def test_cluster_widths(eat, width):
     assert np.array_equal(got, case.oracle_rows(q.source, q.t_s))
 
 
-def test_large_network_sampled(eat):
-    """200,000-stop network, about 46 M connections, 1,024 queries in one launch; sampled rows
-    are compared with the oracle exactly and more rows are certified."""
-    tt = synth.large()
-    case = Case(eat, tt)
+def test_large_network_all_rows(eat, large_tt, large_sc):
+    """200,000-stop network, about 46 M connections, 1,024 queries in one launch: every row
+    equals the oracle's, with the library's default launch and 60-minute clusters, and with
+    30-minute clusters in the launch shape the autotuner picks (the benchmark's setup)."""
+    import os
+    tt = large_tt
     q = synth.random_queries(tt, 1024, 0x1A)
-    got, status, cnt = case.run(eat, q.source, q.t_s)
-    assert (status == 0).all()
-    idx = np.random.default_rng(0).choice(1024, 12, replace=False)
-    want = case.oracle_rows(q.source[idx], q.t_s[idx])
-    assert np.array_equal(got[idx], want)
-    for i in np.random.default_rng(1).choice(1024, 4, replace=False):
-        assert oracle.certify(tt, int(q.source[i]), int(q.t_s[i]), got[i]) == (0, -1)
+    want, _ = oracle.csa_many(large_sc, q.source, q.t_s, os.cpu_count() or 8)
+    for width, tune in ((3600, False), (1800, True)):
+        net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=0, cluster_width=width)
+        if tune:
+            sample = synth.random_queries(tt, 1024, 0x1A - 1)
+            eat.eat_autotune(net, _dev(sample.source), _dev(sample.t_s))
+        out = torch.empty(1024 * tt.n_stops, dtype=torch.int32, device="cuda")
+        status = torch.full((1024,), -1, dtype=torch.int32, device="cuda")
+        eat.eat_query_batch(net, _dev(q.source), _dev(q.t_s), out, status=status)
+        torch.cuda.synchronize()
+        assert (status.cpu().numpy() == 0).all()
+        got = out.view(1024, tt.n_stops).cpu().numpy()
+        bad = np.nonzero((got != want).any(axis=1))[0]
+        assert bad.size == 0, (width, bad[:8])
+        del out
+        net.close()
+    for i in (0, 511, 1023):
+        assert oracle.certify(tt, int(q.source[i]), int(q.t_s[i]), want[i]) == (0, -1)
+
+
+def test_ragged_64_networks_4096_queries(eat):
+    """The ragged workload at full size: 64 grid networks of 1,000-50,000 stops and 4,096
+    queries over them in one eat_query_batch_multi launch (the benchmark's first timed
+    batch, default launch shape); every row equals the oracle's."""
+    import os
+    tts = synth.ragged_grids(64)
+    nets = [eat.eat_build(t.n_stops, t.u, t.v, t.dep, t.dur, device=0, cluster_width=1800)
+            for t in tts]
+    Q = 4096
+    qs = synth.random_queries(tts, Q, 0xA0 + 5)
+    sizes = np.array([tts[i].n_stops for i in qs.net], np.int64)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    out = torch.full((int(sizes.sum()),), -7, dtype=torch.int32, device="cuda")
+    status = torch.full((Q,), -1, dtype=torch.int32, device="cuda")
+    eat.eat_query_batch_multi(nets, _dev(qs.net), _dev(qs.source), _dev(qs.t_s), out,
+                              torch.as_tensor(offs).cuda(), status=status)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    flat = out.cpu().numpy()
+    threads = os.cpu_count() or 8
+    for j, tt in enumerate(tts):
+        sel = np.nonzero(qs.net == j)[0]
+        if sel.size == 0:
+            continue
+        want, _ = oracle.csa_many(oracle.SortedConnections(tt), qs.source[sel], qs.t_s[sel], threads)
+        for r, i in enumerate(sel):
+            assert np.array_equal(flat[offs[i]:offs[i] + tt.n_stops], want[r]), (j, i)
+    for n in nets:
+        n.close()
 
 
 @pytest.mark.parametrize("scheme", [1, 2])

@@ -77,3 +77,40 @@ def test_cuda_graph_capture_and_replay(eat):
         torch.cuda.synchronize()
         want, _ = oracle.csa_many(sc, q.source, q.t_s, 8)
         assert np.array_equal(out.view(n, V).cpu().numpy(), want)
+
+
+def test_autotune_multi_over_ragged_networks(eat):
+    """eat_autotune_multi picks a shape and start order for a batch over networks of uneven
+    size; a launch with that shape gives the oracle's rows."""
+    tts = [synth.small_grid()] + [synth.grid_timetable(n, int(np.ceil(50 * n / 1024)), 600 + n,
+                                                       force_stop0=False) for n in (2000, 9000)]
+    nets = [eat.eat_build(t.n_stops, t.u, t.v, t.dep, t.dur, device=0) for t in tts]
+    Q = 512
+    qs = synth.random_queries(tts, Q, 0xA9)
+    shape = eat.eat_autotune_multi(nets, _dev(qs.net), _dev(qs.source), _dev(qs.t_s))
+    assert shape["block"] in (256, 512, 1024) and shape["vwarp"] in (2, 4, 8, 16, 32)
+    assert shape["mode"] in (1, 3)
+    assert shape["order"] in (eat.EAT_ORDER_BY_TIME, eat.EAT_ORDER_AS_GIVEN)
+    assert eat.eat_launch_shape(nets, Q, **shape)["order"] == shape["order"]
+    sizes = np.array([tts[i].n_stops for i in qs.net], np.int64)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    out = torch.full((int(sizes.sum()),), -7, dtype=torch.int32, device="cuda")
+    status = torch.full((Q,), -1, dtype=torch.int32, device="cuda")
+    eat.eat_query_batch_multi(nets, _dev(qs.net), _dev(qs.source), _dev(qs.t_s), out,
+                              torch.as_tensor(offs).cuda(), status=status, **shape)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    flat = out.cpu().numpy()
+    for j, tt in enumerate(tts):
+        sel = np.nonzero(qs.net == j)[0]
+        want, _ = oracle.csa_many(oracle.SortedConnections(tt), qs.source[sel], qs.t_s[sel], 8)
+        for r, i in enumerate(sel):
+            assert np.array_equal(flat[offs[i]:offs[i] + tt.n_stops], want[r]), (j, i)
+    for order in (eat.EAT_ORDER_BY_TIME, eat.EAT_ORDER_AS_GIVEN):
+        out2 = torch.full_like(out, -7)
+        eat.eat_query_batch_multi(nets, _dev(qs.net), _dev(qs.source), _dev(qs.t_s), out2,
+                                  torch.as_tensor(offs).cuda(), order=order)
+        torch.cuda.synchronize()
+        assert torch.equal(out, out2)
+    with pytest.raises(eat.EatError):
+        eat.eat_autotune_multi(nets, qs.net, qs.source, qs.t_s)        # host arrays
