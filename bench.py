@@ -64,7 +64,7 @@ BYTES = {"vertices": 20, "types": 28, "aps": 16, "relaxed": 12}
 NCU_TRAFFIC_PER_QUERY = {"city": ("aee99e7763a75c69", "eat_cta_kernel", 62338560 / 256),
                          "large": ("aee99e7763a75c69", "eat_cta_kernel", 2690225104 / 152)}
 KERNEL_OF_MODE = {1: "eat_cta_kernel", 2: "eat_cluster_kernel", 3: "eat_async_kernel",
-                  4: "eat_pair_kernel"}
+                  4: "eat_pair_kernel", 5: "eat_cta_kernel"}
 
 
 def kernel_hash() -> str:
@@ -261,7 +261,9 @@ def run_ours_ragged(args):
 
 
 def run_serve(args):
-    """Served queries: city network + 16 small grids resident; Poisson arrivals."""
+    """Served queries: city network + 16 small grids resident; Poisson arrivals.  Rows of a
+    1 % sample are kept and compared with the oracle after each rate's run, outside the
+    submit/poll loop."""
     import torch
     import oracle
     from paper_1912_00966_gb300 import eat
@@ -277,28 +279,28 @@ def run_serve(args):
     results = []
     for rate in args.serve_rates:
         server = eat.Server(nets, max_batch=args.serve_batch, max_inflight=4,
-                            batch_wait_us=args.serve_wait_us)
+                            batch_wait_us=args.serve_wait_us, admission=args.serve_admission)
         rng = np.random.default_rng(rate)
         n = int(rate * args.serve_seconds)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
         qs = synth.random_queries(tts, n, 0x5E + rate)
         pool = {j: [np.empty(tts[j].n_stops, np.int32) for _ in range(64)] for j in range(len(tts))}
         inflight = {}
-        lat, lag, checked, bad = [], [], 0, 0
+        kept = {}                     # the 1 % sample's rows, checked after the run
+        lat, lag, bad_status = [], [], 0
         done = 0
 
         def drain(timeout_us):
-            nonlocal done, checked, bad
+            nonlocal done, bad_status
             for tag, status, net, l_ns in server.poll(timeout_us=timeout_us):
                 buf = inflight.pop(tag)
                 lat.append(l_ns / 1e6)
                 if status != 0:
-                    bad += 1
-                elif tag % 100 == 0:
-                    want = oracle.csa(scs[net], int(qs.source[tag]), int(qs.t_s[tag]))
-                    checked += 1
-                    bad += int(not np.array_equal(buf, want))
-                pool[net].append(buf)
+                    bad_status += 1
+                if tag % 100 == 0:
+                    kept[tag] = buf
+                else:
+                    pool[net].append(buf)
                 done += 1
 
         t0 = time.perf_counter()
@@ -320,20 +322,26 @@ def run_serve(args):
         wall = time.perf_counter() - t0
         st = server.stats()
         server.close()
+        mismatches = 0
+        for tag, buf in kept.items():
+            want = oracle.csa(scs[int(qs.net[tag])], int(qs.source[tag]), int(qs.t_s[tag]))
+            mismatches += int(not np.array_equal(buf, want))
         results.append({
             "offered_qps": rate, "seconds": args.serve_seconds, "requests": n,
             "sustained_qps": n / wall, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(np.max(lat)),
             "submit_lag_p99_ms": float(np.percentile(lag, 99)),
-            "batches": st["batches"], "mean_batch": st["batched_queries"] / max(1, st["batches"]),
-            "max_inflight_batches": st["max_inflight_seen"], "checked_vs_oracle": checked,
-            "mismatches": bad,
+            "launches": st["batches"], "admitted_into_running_launch": st["admitted_running"],
+            "max_on_gpu": st["max_inflight_seen"], "ring_or_slots": st["slots"],
+            "checked_vs_oracle": len(kept), "mismatches": mismatches, "bad_status": bad_status,
         })
     line = {
         "metric": "EAT serving latency and sustained queries/s", "unit": "ms / queries/s",
         "n_gpus": 1, "higher_is_better": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": "serve: city20k network + 16 grid1024 networks resident; "
                                "Poisson arrivals, random network / source / t_s",
+                   "admission": {0: "ring (requests join the running launch)",
+                                 1: "batches per slot"}[args.serve_admission],
                    "max_batch": args.serve_batch, "slots": 4,
                    "batch_wait_us": args.serve_wait_us, "cluster_width_s": args.cluster_width},
         "rates": results, "kernel_hash": kernel_hash(),
@@ -504,14 +512,14 @@ def cpu_oracle_latency(tt, src, ts, budget_s, max_q=64):
 
 
 LADDER_NAMES = {1: "Connection (Algorithm 4)", 2: "Connection-Type (Algorithm 5)",
-                3: "Connection-Type-AP (Algorithm 6)", 4: "Cluster-AP (Section III-D)",
-                5: "Edge (Section III-E)", 6: "Warps (Section III-F)"}
+                3: "Connection-Type-AP (Algorithm 6)", 4: "Cluster-AP (Section II-D)",
+                5: "Edge (Section II-E)", 6: "Warps (Section II-F)"}
 
 
 def run_ladder(args):
     """Single-query latency of the paper's topology-driven variants (Table II's ladder, on
     the synthetic city network), with the flag read after every round and every
-    ceil(sqrt(d)) rounds (Section V-D), each with one launch per round and with the rounds
+    ceil(sqrt(d)) rounds (Section IV-C), each with one launch per round and with the rounds
     between flag reads replayed as a CUDA graph, beside the frontier-driven kernel and the
     oracle."""
     import torch
@@ -576,7 +584,7 @@ def run_ladder(args):
     for r in rows:
         r["speedup_vs_oracle_single_thread"] = None if cpu_ms is None else cpu_ms / r["ms_per_query"]
     line = {
-        "metric": "EAT single-query latency by variant (the ladder of Section III, Table II)",
+        "metric": "EAT single-query latency by variant (the ladder of Section II, Table II)",
         "unit": "ms/query", "n_gpus": 1, "higher_is_better": False, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": describe("city", tt, n_q)["workload"], "queries": n_q,
@@ -736,7 +744,7 @@ def run_ours(args):
         eat.eat_query_batch(net, src_h[i], ts_h[i], out_h, stream=stream, **opts)
         e2e_t.append(time.perf_counter() - t0)
 
-    # The same steps on the network without sub-trips (Section III-G off), for comparison.
+    # The same steps on the network without sub-trips (Section II-G off), for comparison.
     base_ms = None
     if args.subtrips:
         net0 = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=dev,
@@ -858,20 +866,23 @@ def main():
     ap.add_argument("--workload", default="large",
                     choices=["city", "small", "large", "ragged", "serve", "ladder"])
     ap.add_argument("--serve-rates", type=int, nargs="+", default=[1000, 5000, 20000, 50000])
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-admission", type=int, default=0, choices=[0, 1],
+                    help="serving: 0 ring (requests join the running launch), 1 batches per slot")
     ap.add_argument("--serve-batch", type=int, default=256)
     ap.add_argument("--serve-wait-us", type=int, default=200)
     ap.add_argument("--plain-queries", type=int, default=4096,
                     help="ragged workload: sequential single queries timed for comparison")
     ap.add_argument("--vwarp", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
-    ap.add_argument("--mode", type=int, default=0, help="0 auto, 1 rounds, 3 asynchronous")
+    ap.add_argument("--mode", type=int, default=0,
+                    help="0 auto, 1 rounds, 3 asynchronous, 4 paired, 5 edge min + degree mapping")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--cluster-width", type=int, default=1800,
-                    help="seconds per departure cluster (Section III-D uses one hour; Section V-B finds narrower clusters faster)")
+                    help="seconds per departure cluster (Section II-D uses one hour; Section IV-B finds narrower clusters faster)")
     ap.add_argument("--subtrips", type=int, default=0, choices=[0, 1, 2],
-                    help="sub-trip shortcuts (Section III-G): 0 none, 1 sqrt(k), 2 sqrt(mean)")
+                    help="sub-trip shortcuts (Section II-G): 0 none, 1 sqrt(k), 2 sqrt(mean)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=0,
                     help="--impl reference: queries of each step the oracle runs (default: 64 "

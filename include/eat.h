@@ -4,18 +4,18 @@
  *
  * Method: "GPU Algorithm for Earliest Arrival Time Problem in Public Transport
  * Networks" (arXiv 1912.00966).
- *   - Problem (Section I and Section II, Preliminaries): a connection
+ *   - Problem (Section I and Section I-A, Preliminaries): a connection
  *     (u, v, t, lambda) leaves stop u at time t and reaches v at t + lambda.
  *     For a query (s, t_s), e[v] is the earliest arrival at v over
  *     time-respecting paths that leave s at or after t_s; e[s] = t_s.
- *   - Data structure (Section IV-A): connections of one edge (u, v) with one
- *     duration form a connection type (Section III-B); each type's departures
+ *   - Data structure (Section III-A): connections of one edge (u, v) with one
+ *     duration form a connection type (Section II-B); each type's departures
  *     are split into clusters of `cluster_width` seconds (one hour in the
- *     paper, Section III-D) and each cluster is stored as arithmetic
- *     progressions (Section II, Arithmetic Progression Technique; Section III-C).
- *   - Query (Algorithms 2, 3 and 5 with the Cluster-AP lookup of Section III-D,
- *     the double-buffered activity of Section IV-B and atomicMin of Section
- *     IV-C): rounds relax the connection types whose tail stop improved in the
+ *     paper, Section II-D) and each cluster is stored as arithmetic
+ *     progressions (Section I-A, Arithmetic Progression Technique; Section II-C).
+ *   - Query (Algorithms 2, 3 and 5 with the Cluster-AP lookup of Section II-D,
+ *     the double-buffered activity of Section III-B and atomicMin of Section
+ *     III-C): rounds relax the connection types whose tail stop improved in the
  *     previous round until no arrival changes.
  *
  * Conventions
@@ -26,7 +26,8 @@
  *   - "device memory" means memory of the network's CUDA device (cudaMalloc,
  *     torch CUDA tensors); "host memory" is ordinary or pinned CPU memory.
  *     Entry points that accept either detect the kind with
- *     cudaPointerGetAttributes.
+ *     cudaPointerGetAttributes; a buffer in device memory of another device is
+ *     refused with EAT_ERR_INVALID.
  *   - Streams are passed as `void *` holding a cudaStream_t (NULL = the
  *     legacy default stream).
  */
@@ -56,10 +57,10 @@ enum eat_status {
 typedef struct eat_net eat_net;
 
 /* Input timetable: n_conn connections as four parallel int32 arrays in host
- * memory (Section II, Preliminaries).  Requirements, checked by eat_build:
+ * memory (Section I-A, Preliminaries).  Requirements, checked by eat_build:
  * 0 <= u, v < n_stops; 1 <= dur < 2^24; dep >= t0 (see eat_build_opts);
  * dep + dur < INT32_MAX.  Identical connections are merged.
- * `trip` (nullable) gives each connection's trip (vehicle run, Section III-G);
+ * `trip` (nullable) gives each connection's trip (vehicle run, Section II-G);
  * connections with a negative trip id belong to no trip.  The connections of a
  * trip, ordered by departure, must form a time-respecting chain (each one leaves
  * the stop the previous one reached, no earlier than it arrived). */
@@ -73,7 +74,7 @@ typedef struct {
     const int32_t *trip;
 } eat_connections;
 
-/* Sub-trip data enhancement (Section III-G). */
+/* Sub-trip data enhancement (Section II-G). */
 enum eat_subtrips {
     EAT_SUBTRIPS_NONE = 0,
     EAT_SUBTRIPS_SQRT_K = 1,     /* trip of k connections: sub-trips of round(sqrt(k)) */
@@ -82,7 +83,7 @@ enum eat_subtrips {
 
 /* Build options.  Zero-initialise for the paper's defaults. */
 typedef struct {
-    int32_t cluster_width; /* seconds per cluster, 1..65535; 0 = 3600 (Section III-D) */
+    int32_t cluster_width; /* seconds per cluster, 1..65535; 0 = 3600 (Section II-D) */
     int32_t t0;            /* start of cluster 0; departures must be >= t0; default 0 */
     int32_t device;        /* CUDA device ordinal; -1 = host-only build (inspection only) */
     int32_t subtrips;      /* EAT_SUBTRIPS_*; needs conn->trip */
@@ -91,11 +92,11 @@ typedef struct {
 /* Sizes of a built network. */
 typedef struct {
     int32_t n_stops;
-    int32_t n_types;        /* connection types C_{u,v,lambda} (Section III-B) */
+    int32_t n_types;        /* connection types C_{u,v,lambda} (Section II-B) */
     int32_t n_edges;        /* distinct (u, v) pairs with connections */
     int32_t cluster_width;
     int32_t t0;
-    int32_t max_clusters;   /* y of Section IV-A: clusters spanned by the widest type */
+    int32_t max_clusters;   /* y of Section III-A: clusters spanned by the widest type */
     int32_t max_out_types;  /* largest number of types leaving one stop */
     int32_t device;         /* -1 for a host-only build */
     int64_t n_conn;         /* connections after merging identical ones */
@@ -104,11 +105,11 @@ typedef struct {
     int64_t device_bytes;   /* bytes of the resident device copy */
     int32_t k_min;          /* device layout: first cluster index stored */
     int32_t y;              /* device layout: clusters stored per type (the paper's y) */
-    int64_t n_ap_extra;     /* device layout: APs beyond the two kept in a cluster entry */
-    int64_t n_shortcuts;    /* artificial sub-trip connections added (Section III-G) */
+    int64_t n_ap_extra;     /* device layout: APs beyond the four kept in a cluster entry */
+    int64_t n_shortcuts;    /* artificial sub-trip connections added (Section II-G) */
 } eat_stats;
 
-/* Read-only host view of the built arrays (Section IV-A's CT[], CL[], AP[], in
+/* Read-only host view of the built arrays (Section III-A's CT[], CL[], AP[], in
  * this library's layout).  Valid until eat_free.
  *   row_ptr [n_stops + 1]: types leaving stop u are row_ptr[u] .. row_ptr[u+1]-1,
  *                          ordered by (v, lambda).
@@ -127,18 +128,21 @@ typedef struct {
     const int32_t *type_cl;
     const int32_t *cl;
     const uint32_t *ap;
-    /* The device layout, derived from the arrays above (Section IV-A's CL stride y):
+    /* The device layout, derived from the arrays above (Section III-A's CL stride y):
      *   cluster_entries[8 * y * n_types]  entry (t, k) for cluster k_min + k at
-     *       record k * n_types + t (cluster-major), one 32-byte record: {rel0 | rel1 << 16, sc0, sc1, next, x/2 | n << 24, v,
-     *       lambda | d << 24, row_ptr[v]}: the cluster's n APs, the first two inline
-     *       with first terms base + rel, base = t0 + (k_min + k) * cluster_width, and
-     *       sc = difference << 16 | terms, the others at ap_extra[x ..] (n = 255: the
-     *       count is the first of two header slots there); next = first departure of
-     *       the next non-empty cluster, EAT_INF if none; v, lambda: head stop and
-     *       duration of type t; d: types leaving v (255: see row_ptr)
-     *   ap_extra[2 * n_ap_extra] */
+     *       record k * n_types + t (cluster-major), one 32-byte record:
+     *       {rel0 | rel1 << 16, sc0, sc1, next, x/2 | n << 24, rel2 | rel3 << 16, sc2, sc3}:
+     *       the cluster's n APs, the first four inline with first terms base + rel,
+     *       base = t0 + (k_min + k) * cluster_width, and sc = difference << 16 | terms,
+     *       the others at ap_extra[x ..] (n = 255: the count is the first of two header
+     *       slots there); next = first departure of the next non-empty cluster,
+     *       EAT_INF if none
+     *   ap_extra[2 * n_ap_extra]
+     *   type_records[4 * n_types]  per type {v, lambda | d << 24, row_ptr[v], last
+     *       departure}: head stop, duration, types leaving v (255: see row_ptr) */
     const int32_t *cluster_entries;
     const uint32_t *ap_extra;
+    const int32_t *type_records;
 } eat_net_view;
 
 /* Per-query work counters (optional output of the query calls). */
@@ -147,11 +151,11 @@ typedef struct {
     int64_t vertices;  /* active stops expanded, summed over rounds (a stop with no
                           outgoing connection never needs expanding) */
     int64_t types;     /* connection types examined with an active tail: the
-                          "connections processed" of Section V-C */
+                          "connections processed" of Section IV-C */
     int64_t evals;     /* of the looked-up types, those with a departure at or after
                           e[u] (their e[v] is read) */
     int64_t lookups;   /* of the examined types, those whose cluster entry was read
-                          (Section III-D); types >= lookups >= evals */
+                          (Section II-D); types >= lookups >= evals */
     int64_t aps;       /* AP records examined by the cluster lookup (Algorithm 6) */
     int64_t relaxed;   /* successful lowerings of some e[v] (Algorithm 3) */
 } eat_counters;
@@ -230,7 +234,16 @@ enum eat_mode {
                            one query converges its threads go to the other and the slot
                            takes the next query.  EAT_MODE_AUTO uses it only where
                            eat_autotune chose it; never in eat_query_batch_noalloc
-                           unless requested */
+                           unless requested */,
+    EAT_MODE_EDGE = 5   /* as EAT_MODE_CTA with two changes (the mapping chosen by degree
+                           and the warp min of Section II-F's warps): a stop with at least
+                           vwarp outgoing connection types is queued whole and expanded
+                           by a sub-warp of vwarp lanes (the whole warp for vwarp 32)
+                           instead of one item per type; and the lanes of a warp whose
+                           types share a head stop v reduce their candidates with a warp
+                           min, so that one lane per head stop reads e[v], lowers it and
+                           pushes v.  EAT_MODE_AUTO uses it only where eat_autotune
+                           chose it */
 };
 
 /* Error message of the calling thread's last failed call ("" if none). */
@@ -241,14 +254,14 @@ int32_t eat_version(void);
 
 /*
  * eat_build -- preprocess a timetable into the Cluster-AP layout and upload it.
- * Section IV-A (graph representation and preprocessing): group connections by
- * edge and duration into connection types (Section III-B), split each type by
- * departure time into clusters of cluster_width seconds (Section III-D), cover
- * each cluster by the greedy AP cover (Section II; Section III-C), order the
+ * Section III-A (graph representation and preprocessing): group connections by
+ * edge and duration into connection types (Section II-B), split each type by
+ * departure time into clusters of cluster_width seconds (Section II-D), cover
+ * each cluster by the greedy AP cover (Section I-A; Section II-C), order the
  * APs of a cluster by first term.  With opts->subtrips, each trip is first cut
  * into consecutive sub-trips and one artificial connection is added per
  * sub-trip of two or more connections, from its first stop at its first
- * departure to its last stop at its last arrival (Section III-G); earliest
+ * departure to its last stop at its last arrival (Section II-G); earliest
  * arrival times are unchanged.
  *   conn  host arrays, read only during the call (copied).
  *   opts  may be NULL (defaults).
@@ -259,19 +272,19 @@ int32_t eat_version(void);
 int eat_build(const eat_connections *conn, const eat_build_opts *opts, eat_net **out);
 
 /* Pre-encoded input for eat_build_csr: the Cluster-AP structure itself (Section
- * IV-A) for callers that encode their own timetable.  All arrays are host memory.
+ * III-A) for callers that encode their own timetable.  All arrays are host memory.
  *   row_ptr[n_stops + 1]   types leaving stop u are row_ptr[u] .. row_ptr[u+1]-1
  *                          (row_ptr[0] = 0, row_ptr[n_stops] = n_types)
  *   type_v[n_types], type_dur[n_types]   head stop and duration (1 .. 2^24-1) of each
- *                          connection type (Section III-B)
+ *                          connection type (Section II-B)
  *   type_cl_ptr[n_types + 1]   clusters of type t are type_cl_ptr[t] ..
  *                          type_cl_ptr[t+1]-1; every type has at least one
  *   cl_k[n_clusters]       cluster index k: the cluster holds departures in
- *                          [t0 + k * width, t0 + (k+1) * width) (Section III-D);
+ *                          [t0 + k * width, t0 + (k+1) * width) (Section II-D);
  *                          strictly increasing within a type
  *   cl_ap_ptr[n_clusters + 1]   APs of cluster c are cl_ap_ptr[c] .. cl_ap_ptr[c+1]-1;
  *                          every cluster has at least one
- *   ap_first[n_aps], ap_step[n_aps], ap_count[n_aps]   AP runs (Section II): terms
+ *   ap_first[n_aps], ap_step[n_aps], ap_count[n_aps]   AP runs (Section I-A): terms
  *                          first, first + step, ..., first + (count-1) * step, all
  *                          inside the cluster's window; count >= 1, step >= 1 when
  *                          count >= 2, step and count <= 65535; ordered by first
@@ -294,7 +307,7 @@ typedef struct {
 
 /*
  * eat_build_csr -- build a network from pre-encoded connection types, clusters
- * and AP runs (the layout of Section IV-A) instead of raw connections.  The
+ * and AP runs (the layout of Section III-A) instead of raw connections.  The
  * input is validated and copied; opts->cluster_width and opts->t0 give the
  * cluster windows (opts->subtrips must be EAT_SUBTRIPS_NONE).  Queries behave
  * exactly as on a network built by eat_build from the connections the APs
@@ -315,7 +328,7 @@ int eat_get_stats(const eat_net *net, eat_stats *out);
 int eat_net_host_view(const eat_net *net, eat_net_view *out);
 
 /*
- * eat_query -- one query (s, t_s), blocking (Algorithms 2-5, Section III-D).
+ * eat_query -- one query (s, t_s), blocking (Algorithms 2-5, Section II-D).
  *   arr_out  [n_stops] int32, host or device memory: arr_out[v] = e[v],
  *            EAT_INF if v is unreachable; arr_out[s] = t_s.  Page-locked host
  *            memory is written in place when the arrivals fit in shared memory.
@@ -400,7 +413,7 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
 /*
  * eat_next_departure -- the Cluster-AP lookup alone (getConnection with
  * getConnectionFromAPs, Algorithm 6, inside the hourly cluster of Section
- * III-D): for each i, out[i] = least departure >= times[i] of connection type
+ * II-D): for each i, out[i] = least departure >= times[i] of connection type
  * types[i], or EAT_INF if there is none.  Exposes the kernel's lookup for
  * testing.  types, times, out: [n] int32 device memory.  Asynchronous on stream.
  * Errors: EAT_ERR_INVALID (type index out of range), EAT_ERR_NO_DEVICE,
@@ -412,13 +425,13 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
 /*
  * eat_autotune -- choose the launch shape for this network by measurement (no
  * counterpart in the paper, which fixes one thread per type or per edge and
- * sweeps the virtual-warp size by hand, Section V-B).  Candidates, in this
+ * sweeps the virtual-warp size by hand, Section IV-B).  Candidates, in this
  * order: block sizes 512, 1024 and 256 threads, each with the round-based mode
  * and vwarp 8, 4, 16, 2, 32 lanes per spilled stop, then with the asynchronous
- * mode, as far as they fit the device (1024 threads first on networks of 8,192
- * stops or more and for batches of at most one query per SM, where it is the
- * default); when n exceeds the SM count, then the paired mode with vwarp 8, 4
- * and 16.  They are run on the sample batch
+ * mode, then with EAT_MODE_EDGE and vwarp 8 and 32, as far as they fit the device
+ * (1024 threads first on networks of 8,192 stops or more and for batches of at most
+ * one query per SM, where it is the default); when n exceeds the SM count, then the
+ * paired mode with vwarp 8, 4 and 16.  They are run on the sample batch
  * sources/times (n queries, device memory) in nine rounds over all candidates:
  * the first warms up, the other eight are timed with CUDA events on `stream`,
  * each after a write of twice the L2 size so that every timing starts with the
@@ -441,7 +454,8 @@ int eat_autotune(eat_net *net, const int32_t *sources, const int32_t *times, int
  * paper, as for eat_autotune.  Candidates, in this order: start order as given, then by
  * t_s (EAT_ORDER_AS_GIVEN, EAT_ORDER_BY_TIME); for each, block sizes 512, 1024 and 256
  * threads, each with the round-based mode and vwarp 8, 4, 16, 2, 32, then the
- * asynchronous mode; shapes without a plan for these networks are skipped.  They run on
+ * asynchronous mode, then EAT_MODE_EDGE with vwarp 8; shapes without a plan for these
+ * networks are skipped.  They run on
  * the sample batch (net_idx, sources, times: [n] int32 device memory; rows packed in
  * query order in a scratch buffer) and are timed as eat_autotune times them (nine rounds,
  * cold L2, median, earliest within 5 % wins).  Nothing is stored in the networks: the
@@ -459,24 +473,48 @@ int eat_autotune_multi(const eat_net *const *nets, int32_t n_nets, const int32_t
  * A request loop with continuous batching over resident networks (no
  * counterpart in the paper, which runs one query at a time; each request runs
  * the same algorithm as eat_query).  Requests for any of the server's networks
- * are queued by eat_server_submit; a dispatcher thread keeps a pool of slots,
- * each a CUDA stream with pre-allocated device buffers for max_batch queries.
- * The pool size is set by mem_budget (admission by device memory: a request is
- * admitted to the GPU only when a slot is free).  A free slot takes up to
- * max_batch pending requests of any networks and runs them as one
- * eat_query_batch_multi launch; batches started while others run overlap on
- * the device.  When a batch finishes, each caller's row is written to its
- * arr_out and a result (tag, status, latency) is queued for eat_server_poll.
+ * are queued by eat_server_submit and a dispatcher thread admits them to the GPU
+ * as memory frees up.  When a request's row is in place it is copied to the
+ * caller's arr_out and a result (tag, status, latency) is queued for
+ * eat_server_poll.  Two admission modes (eat_server_opts.admission):
+ *
+ *   EAT_ADMIT_RING (default): one persistent launch of the per-query kernel (one
+ *     query per thread block, all blocks the SMs hold) serves a ring of requests in
+ *     page-locked host memory.  The dispatcher writes each admitted request into a
+ *     free ring entry and publishes it; a block that finishes its query takes the
+ *     next published request at once, while the launch runs, so a request that
+ *     arrives while others are on the GPU starts as soon as one block is free.  The
+ *     block writes the arrival row into the entry's row of a page-locked pool in
+ *     place and marks the entry done.  The ring's capacity (requests on the GPU at
+ *     once) is set by mem_budget (admission by memory: a request enters the ring
+ *     only when an entry and its row are free), at most max_batch * max_inflight.
+ *     The launch ends when the dispatcher has had no request in flight for about
+ *     2 ms (it sets a stop flag that idle blocks read); a later request starts a
+ *     new launch.  Every wait of a block is bounded (about 100 ms without a
+ *     request, then it leaves).  Needs the networks' frontier bitmaps to fit in
+ *     shared memory (up to about 900,000 stops).
+ *   EAT_ADMIT_BATCH: a pool of slots, each a CUDA stream with pre-allocated device
+ *     buffers for max_batch queries (the pool size set by mem_budget).  A free slot
+ *     takes up to max_batch pending requests of any networks and runs them as one
+ *     eat_query_batch_multi launch; batches started while others run overlap on the
+ *     device, and a request that arrives while all slots run waits for a slot.
  * The networks must stay alive until eat_server_destroy. */
 typedef struct eat_server eat_server;
 
+enum eat_admission {
+    EAT_ADMIT_RING = 0,
+    EAT_ADMIT_BATCH = 1
+};
+
 typedef struct {
-    int32_t max_batch;      /* requests per launch; 0 = 256 */
-    int32_t max_inflight;   /* slots (concurrent launches); 0 = 4 */
-    int32_t batch_wait_us;  /* while another batch runs, wait up to this long for a
-                               fuller batch; 0 = 200 */
-    int32_t reserved;
-    int64_t mem_budget;     /* device + pinned bytes for the slots; 0 = 1 GiB */
+    int32_t max_batch;      /* EAT_ADMIT_BATCH: requests per launch; 0 = 256 */
+    int32_t max_inflight;   /* EAT_ADMIT_BATCH: slots (concurrent launches); 0 = 4.
+                               EAT_ADMIT_RING: ring capacity at most max_batch *
+                               max_inflight, rounded down to a power of two */
+    int32_t batch_wait_us;  /* EAT_ADMIT_BATCH: while another batch runs, wait up to this
+                               long for a fuller batch; 0 = 200 */
+    int32_t admission;      /* EAT_ADMIT_* */
+    int64_t mem_budget;     /* device + pinned bytes for the slots or the ring; 0 = 1 GiB */
 } eat_server_opts;
 
 typedef struct {
@@ -486,12 +524,24 @@ typedef struct {
     int64_t latency_ns;     /* submit to result delivered */
 } eat_server_result;
 
+/* Counters since creation.  batches: launches (EAT_ADMIT_RING: ring launches);
+ * batched_queries: requests admitted to the GPU; max_batch_seen: largest batch
+ * (EAT_ADMIT_RING: most requests in the ring at once); max_inflight_seen: most
+ * batches running at once (EAT_ADMIT_RING: most requests in the ring at once);
+ * slots, slot_bytes: batch slots and bytes per slot (EAT_ADMIT_RING: ring capacity
+ * and bytes per entry with its row); admitted_running: requests admitted while a
+ * launch was already running (EAT_ADMIT_RING: entered the ring of a running
+ * launch); base_bytes: see below.  mem_budget covers base_bytes + slots *
+ * slot_bytes. */
 typedef struct {
     int64_t submitted, completed, pending;
     int64_t batches, batched_queries;
     int64_t max_batch_seen, max_inflight_seen, max_pending_seen;
     int64_t slots, slot_bytes;
     int64_t last_error;
+    int64_t admitted_running;
+    int64_t base_bytes;     /* bytes held besides the slots or ring entries (EAT_ADMIT_RING:
+                               the launch's workspace and device rows) */
 } eat_server_stats;
 
 /* Create a server for nets[0 .. n_nets-1] (same device, 1..EAT_MAX_NETS);
@@ -540,10 +590,13 @@ void eat_server_destroy(eat_server *sv);
  *     contents; the call clears what must start at zero.  Calls whose GPU work
  *     overlaps (on different streams or threads, for any network on the same
  *     device) race on the scratch and give wrong results: serialise them.
- *   - Limit: each concurrently running query needs 8 * n_stops bytes of the
- *     scratch (rounded up), so the network may have at most 2,000,000 stops;
- *     fewer queries then run at once and the rest wait in the same launch.
- *     Larger networks are rejected with EAT_ERR_INVALID.
+ *   - Limit: each persistent thread block needs 8 * n_stops bytes of the scratch
+ *     (rounded up) for its frontier queue, plus n_stops / 4 bytes when the frontier
+ *     bitmaps live in global memory (networks beyond about 900,000 stops), or
+ *     16 * n_stops bytes in the paired mode (two queries per block); the round-free
+ *     mode needs none.  So the network may have at most 2,000,000 stops, and on
+ *     large networks fewer blocks run at once while the other queries wait in the
+ *     same launch.  Larger networks are rejected with EAT_ERR_INVALID.
  * Errors: EAT_ERR_INVALID (host buffers, network too large, bad options),
  * EAT_ERR_NO_DEVICE, EAT_ERR_CUDA.
  */
@@ -554,14 +607,14 @@ int eat_query_batch_noalloc(const eat_net *net, const int32_t *sources, const in
                             void *stream);
 
 /* ------------------------------------------------------------------------
- * Topology-driven variants (Section III-A to III-F), the paper's own execution
+ * Topology-driven variants (Section II-A to II-F), the paper's own execution
  * model, kept as a baseline and to show what each pruning step buys.
  *
  * One query at a time.  Each round one kernel visits every connection, type or
  * edge and works only on those whose tail stop is active, i.e. was improved in
- * the round before (Section IV-B's active / nextactive pair, kept here as two
+ * the round before (Section III-B's active / nextactive pair, kept here as two
  * arrays of round stamps).  The host drives the rounds and reads the device's
- * "improved in round i" flag every `flag_every` rounds (Section V-D: 1 = after
+ * "improved in round i" flag every `flag_every` rounds (Section IV-C: 1 = after
  * every round, as in Algorithms 4-5; about sqrt(d) = the reduced transfer of
  * Table V); the rounds run after convergence find nothing active.
  * ------------------------------------------------------------------------ */
@@ -573,13 +626,13 @@ enum eat_variant {
     EAT_VAR_TYPE = 2,         /* Algorithm 5: one thread per connection type; the
                                  earliest departure >= e[u] by linear search of the
                                  type's sorted departures (getConnection) */
-    EAT_VAR_TYPE_AP = 3,      /* Section III-C: as 2, the departure from the type's
+    EAT_VAR_TYPE_AP = 3,      /* Section II-C: as 2, the departure from the type's
                                  whole-day AP tuples (Algorithm 6) */
-    EAT_VAR_CLUSTER_AP = 4,   /* Section III-D: as 3 inside the cluster of e[u], else
+    EAT_VAR_CLUSTER_AP = 4,   /* Section II-D: as 3 inside the cluster of e[u], else
                                  the next non-empty cluster's first departure */
-    EAT_VAR_EDGE = 5,         /* Section III-E: one thread per edge (u, v), all its
+    EAT_VAR_EDGE = 5,         /* Section II-E: one thread per edge (u, v), all its
                                  types by Cluster-AP */
-    EAT_VAR_WARP = 6          /* Section III-F: one warp per edge, its types spread
+    EAT_VAR_WARP = 6          /* Section II-F: one warp per edge, its types spread
                                  over the lanes, by Cluster-AP */
 };
 
@@ -593,7 +646,7 @@ typedef struct {
  * the Cluster-AP network of eat_build (same options and errors) plus the
  * connections themselves (16 B each), every type's {tail, head, duration},
  * its sorted unique departures and its whole-day greedy AP cover (the cover
- * rule of Section II, as in the clusters, over all of the type's departures:
+ * rule of Section I-A, as in the clusters, over all of the type's departures:
  * first term, difference and terms as int32), and the edges (runs of types
  * with the same tail and head).  Input arrays are copied.  Free with
  * eat_ladder_free.  Errors: as eat_build; EAT_ERR_NO_DEVICE for device < 0.

@@ -9,15 +9,15 @@ Contents, each following the paper:
   * `csa`, `csa_many`: the connection-scan algorithm, Algorithm 1 (C, csa.c).
   * `certify`: exactness certificate for an arrival vector (C, csa.c).
   * `brute.foremost_dijkstra`, `brute.exhaustive_paths`: independent brute force.
-  * `ap_greedy.ap_cover`: greedy AP cover (Section II, Arithmetic Progression
+  * `ap_greedy.ap_cover`: greedy AP cover (Section I-A, Arithmetic Progression
     Technique).
-  * `next_departure`: the plain definition of getConnection (Section III-B):
+  * `next_departure`: the plain definition of getConnection (Section II-B):
     t_c = min{ t : (u, v, t, lambda) in C_{u,v,lambda}, t >= e[u] }.
   * `cluster_sets`: the partition of a connection type into clusters by
     departure time, cluster k holding departures in [t0 + kW, t0 + (k+1)W)
-    (Section III-D with W = 3600 and t0 = 0: departures in [k:00:00, k:59:59]).
+    (Section II-D with W = 3600 and t0 = 0: departures in [k:00:00, k:59:59]).
   * `connection_types`: the partition of C into connection types C_{u,v,lambda}
-    (Section III-B), each type's departures sorted and merged.
+    (Section II-B), each type's departures sorted and merged.
 """
 from __future__ import annotations
 
@@ -119,7 +119,7 @@ def certify(tt, s: int, t_s: int, e) -> tuple[int, int]:
 
 
 def connection_types(tt):
-    """Partition C into connection types C_{u,v,lambda} (Section III-B): connections with
+    """Partition C into connection types C_{u,v,lambda} (Section II-B): connections with
     the same endpoints and duration.  Returns {(u, v, lambda): sorted unique departures}."""
     key = np.stack([tt.u, tt.v, tt.dur], axis=1).astype(np.int64)
     order = np.lexsort((tt.dep, key[:, 2], key[:, 1], key[:, 0]))
@@ -131,7 +131,7 @@ def connection_types(tt):
 
 
 def next_departure(departures, e_u: int) -> int:
-    """getConnection's result (Section III-B): the least departure >= e_u of a type, or INF."""
+    """getConnection's result (Section II-B): the least departure >= e_u of a type, or INF."""
     best = INF
     for t in departures:
         if t >= e_u and t < best:
@@ -141,7 +141,7 @@ def next_departure(departures, e_u: int) -> int:
 
 def cluster_sets(departures, width: int = 3600, t0: int = 0):
     """Split a type's departures into clusters: cluster k holds t with
-    k*width <= t - t0 < (k+1)*width (Section III-D).  Returns {k: sorted list}."""
+    k*width <= t - t0 < (k+1)*width (Section II-D).  Returns {k: sorted list}."""
     out = {}
     for t in departures:
         out.setdefault((int(t) - t0) // width, []).append(int(t))

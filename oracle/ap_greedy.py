@@ -1,10 +1,10 @@
 """Oracle (test infrastructure only): greedy arithmetic-progression cover.
 
-Section II ("Arithmetic Progression Technique", after Bast and Storandt) covers a
+Section I-A ("Arithmetic Progression Technique", after Bast and Storandt) covers a
 set S of departure times by APs: repeatedly take the smallest uncovered a in S,
 choose the longest AP that starts at a, lies inside S and covers the most
 still-uncovered numbers, and mark its terms covered.  An AP is stored as
-(first term, last term, difference); Section III-C adds that expanding all APs of
+(first term, last term, difference); Section II-C adds that expanding all APs of
 a set gives back exactly S, and that the APs are kept in increasing order of
 their first term.
 

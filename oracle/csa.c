@@ -5,7 +5,7 @@
  * Only the tests, the smoke check and the benchmark's CPU-baseline leg may load
  * this file's library.  It shares nothing with the CUDA path.
  *
- * Model (Section II, Preliminaries): a connection (u, v, t, lambda) leaves stop u
+ * Model (Section I-A, Preliminaries): a connection (u, v, t, lambda) leaves stop u
  * at time t and reaches v at t + lambda.  For a query (s, t_s) the earliest
  * arrival time e[v] is the least arrival over time-respecting paths that leave s
  * at or after t_s; e[s] = t_s; unreachable stops keep "infinity", written here as

@@ -1,5 +1,5 @@
 """Autotuning of the query path: launch shape (in libeat, eat_autotune) and the cluster
-width of the build (Section V-B's cluster-size parameter, which needs a rebuild).
+width of the build (Section IV-B's cluster-size parameter, which needs a rebuild).
 
 Everything here measures real launches through the C ABI on a caller's sample batch;
 nothing is computed on the host.

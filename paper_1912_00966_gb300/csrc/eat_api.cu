@@ -47,6 +47,22 @@ static bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory of a device other than dev (the kernels would read or write a foreign
+// address); host, managed and NULL pointers are not foreign.
+static bool foreign_ptr(const void *p, int dev) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device != dev;
+}
+
+static int foreign_fail() {
+    return fail(EAT_ERR_INVALID, "a buffer is device memory of another device than the network's");
+}
+
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Device address of page-locked host memory that the GPU may read and write in place
@@ -128,6 +144,7 @@ struct Plan {
     int cluster = 0;              // blocks per query in cluster mode (EAT_MODE_CLUSTER), else 0
     bool pack = false;            // one int32 per queued item (small networks, shared arrivals)
     bool pair = false;            // two queries per block (EAT_MODE_PAIR)
+    bool edge = false;            // warp min per head stop, degree-chosen mapping (EAT_MODE_EDGE)
     bool order = false;           // queries start by t_s (EAT_ORDER_BY_TIME): order array at off_order
     size_t off_order = 0;
 };
@@ -325,8 +342,10 @@ static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const ea
     while ((1 << l) < vw) ++l;
     if ((1 << l) != vw || vw > 32) return fail(EAT_ERR_INVALID, "vwarp must be 1, 2, 4, 8, 16 or 32");
     p.vw_log2 = l;
-    if (o && (o->mode < EAT_MODE_AUTO || o->mode > EAT_MODE_PAIR))
+    if (o && (o->mode < EAT_MODE_AUTO || o->mode > EAT_MODE_EDGE))
         return fail(EAT_ERR_INVALID, "mode must be one of EAT_MODE_*");
+    p.edge = (o && o->mode == EAT_MODE_EDGE) ||
+             (tm == EAT_MODE_EDGE && !(o && o->mode != EAT_MODE_AUTO));
     if (o && o->mode == EAT_MODE_PAIR) {
         if (n_nets != 1) return fail(EAT_ERR_INVALID, "paired mode serves one network per launch");
         if (o->placement != EAT_PLACE_AUTO && o->placement != EAT_PLACE_SHARED)
@@ -503,6 +522,7 @@ static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net
     qa.spec = 0;
     qa.idle_cap = kDefaultIdleCap;
     qa.rg = RingArgs{};
+    qa.edge = p.edge ? 1 : 0;
     return qa;
 }
 
@@ -583,6 +603,82 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
     return EAT_OK;
 }
 
+// Launch shape of the serving ring kernel: the round-based per-query kernel with the
+// default shape of a full batch over these networks (all blocks the SMs hold),
+// frontier bitmaps in shared memory.
+int ring_setup(const eat_net *const *nets, int n_nets, RingLaunch &rl) {
+    int32_t vmax = 0, vmin = INT32_MAX;
+    for (int i = 0; i < n_nets; ++i) {
+        vmax = std::max(vmax, nets[i]->host.n_stops);
+        vmin = std::min(vmin, nets[i]->host.n_stops);
+    }
+    DeviceInfo d;
+    int rc = device_info(nets[0]->device, d);
+    if (rc) return rc;
+    eat_query_opts o{};
+    o.mode = EAT_MODE_CTA;
+    Plan p;
+    rc = make_plan(nets[0]->device, vmax, 4 * d.sms, n_nets, &o, p, vmin, nullptr, false);
+    if (rc) return rc;
+    if (p.mem == 2)
+        return fail(EAT_ERR_INVALID, "ring admission keeps the frontier bitmaps in shared memory; "
+                                     "these networks are too large (use EAT_ADMIT_BATCH)");
+    int per_sm = 0;
+    {
+        DeviceGuard guard(nets[0]->device);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ring_kernel(p.mem),
+                                                                      p.block, p.smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    }
+    if (per_sm < 1) return fail(EAT_ERR_INVALID, "ring kernel does not fit on an SM");
+    rl.mem = p.mem;
+    rl.block = p.block;
+    rl.grid = per_sm * d.sms;
+    rl.smem = p.smem;
+    rl.vmax = p.vmax;
+    rl.vw_log2 = p.vw_log2;
+    rl.qcap = p.qcap;
+    rl.mask_words = p.mask_words;
+    rl.smem_mask_off = p.smem_mask_off;
+    rl.smem_q_off = p.smem_q_off;
+    rl.smem_arr_cap = p.smem_arr_cap;
+    rl.spill_stride = p.spill_stride;
+    rl.ws_bytes = kWsHeader + (size_t)rl.grid * (size_t)p.spill_stride * 4;
+    rl.rows_stride = p.mem == 0 ? 0 : (int64_t)align_up((size_t)p.vmax, 64);
+    rl.rows_bytes = (size_t)rl.grid * (size_t)rl.rows_stride * 4;
+    return EAT_OK;
+}
+
+int ring_launch(const eat_net *const *nets, int n_nets, const RingLaunch &rl, void *ws,
+                int32_t *arr_rows, int32_t *pool, const RingArgs &rg, cudaStream_t st) {
+    Plan p;
+    p.mem = rl.mem;
+    p.block = rl.block;
+    p.vw_log2 = rl.vw_log2;
+    p.vmax = rl.vmax;
+    p.qcap = rl.qcap;
+    p.mask_words = rl.mask_words;
+    p.smem_mask_off = rl.smem_mask_off;
+    p.smem_q_off = rl.smem_q_off;
+    p.smem_arr_cap = rl.smem_arr_cap;
+    p.spill_stride = rl.spill_stride;
+    p.mask_stride = 0;
+    QueryArgs qa = make_args(p, rl.grid, (char *)ws, nullptr, nullptr, nullptr, 0, n_nets, pool,
+                             nullptr, rl.vmax < INT32_MAX ? rl.vmax + 1 : rl.vmax, nullptr, nullptr);
+    qa.spec = spec_items(nets, n_nets) ? 1 : 0;
+    qa.rg = rg;
+    if (rl.mem != 0) {
+        qa.arr_rows = arr_rows;
+        qa.arr_rows_stride = rl.rows_stride;
+    }
+    NetDev devs[EAT_MAX_NETS];
+    for (int i = 0; i < n_nets; ++i) devs[i] = nets[i]->dev;
+    DeviceGuard guard(nets[0]->device);
+    cudaError_t e = launch_ring(devs, n_nets, qa, rl.mem, rl.grid, rl.block, rl.smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ring kernel launch");
+    return EAT_OK;
+}
+
 }  // namespace eat
 
 using namespace eat;
@@ -610,7 +706,8 @@ static int upload(eat_net *net) {
     }
     const HostNet &h = net->host;
     size_t off_row = 0;
-    size_t off_ce = align_up(off_row + ((size_t)h.n_stops + 1) * 4, 256);
+    size_t off_tr = align_up(off_row + ((size_t)h.n_stops + 1) * 4, 256);
+    size_t off_ce = align_up(off_tr + h.tr.size() * 4, 256);
     size_t off_apx = align_up(off_ce + h.ce.size() * 4, 256);
     size_t total = align_up(off_apx + h.apx.size() * 4 + 16, 256);
     DeviceGuard guard(net->device);
@@ -625,6 +722,7 @@ static int upload(eat_net *net) {
     char *b = (char *)net->blob;
     struct Piece { size_t off; const void *src; size_t bytes; } pieces[] = {
         {off_row, h.row_ptr.data(), h.row_ptr.size() * 4},
+        {off_tr, h.tr.data(), h.tr.size() * 4},
         {off_ce, h.ce.data(), h.ce.size() * 4},
         {off_apx, h.apx.data(), h.apx.size() * 4},
     };
@@ -635,6 +733,7 @@ static int upload(eat_net *net) {
     }
     NetDev &d = net->dev;
     d.row_ptr = (const int32_t *)(b + off_row);
+    d.tr = (const int4 *)(b + off_tr);
     d.ce = (const int4 *)(b + off_ce);
     d.apx = (const uint2 *)(b + off_apx);
     d.n_stops = h.n_stops;
@@ -757,6 +856,7 @@ int eat_net_host_view(const eat_net *net, eat_net_view *out) {
     out->ap = net->host.ap.data();
     out->cluster_entries = net->host.ce.data();
     out->ap_extra = net->host.apx.data();
+    out->type_records = net->host.tr.data();
     return EAT_OK;
 }
 
@@ -796,7 +896,7 @@ int eat_launch_shape(const eat_net *const *nets, int32_t n_nets, int32_t n,
     shape->block = p.block;
     shape->vwarp = 1 << p.vw_log2;
     shape->mode = p.cluster ? EAT_MODE_CLUSTER : p.pair ? EAT_MODE_PAIR
-                  : p.async ? EAT_MODE_ASYNC : EAT_MODE_CTA;
+                  : p.async ? EAT_MODE_ASYNC : p.edge ? EAT_MODE_EDGE : EAT_MODE_CTA;
     shape->cluster = p.cluster;
     shape->order = p.order ? EAT_ORDER_BY_TIME : EAT_ORDER_AS_GIVEN;
     return EAT_OK;
@@ -808,6 +908,7 @@ int eat_query(const eat_net *net, int32_t s, int32_t t_s, int32_t *arr_out,
     if (!net || !arr_out) return fail(EAT_ERR_INVALID, "NULL argument");
     if (net->device < 0) return fail(EAT_ERR_NO_DEVICE, "network was built host-only");
     if (s < 0 || s >= net->host.n_stops) return fail(EAT_ERR_INVALID, "source out of range");
+    if (foreign_ptr(arr_out, net->device)) return foreign_fail();
     std::lock_guard<std::mutex> g(net->ws_lock);
     Plan p;
     int rc = make_plan(net->device, net->host.n_stops, 1, 1, nullptr, p, -1, net);
@@ -861,6 +962,9 @@ int eat_query_batch_multi(const eat_net *const *nets, int32_t n_nets, const int3
     if (n < 0) return fail(EAT_ERR_INVALID, "n must be >= 0");
     if (n > 0 && (!net_idx || !sources || !times || !arr_out || !arr_offsets))
         return fail(EAT_ERR_INVALID, "NULL query array");
+    for (const void *b : {(const void *)net_idx, (const void *)sources, (const void *)times,
+                          (const void *)arr_out, (const void *)arr_offsets, (const void *)workspace})
+        if (foreign_ptr(b, nets[0]->device)) return foreign_fail();
     DeviceGuard guard(nets[0]->device);
     cudaStream_t st = (cudaStream_t)stream;
     const bool dev_in = n == 0 || is_device_ptr(sources);
@@ -955,6 +1059,9 @@ int eat_query_batch(const eat_net *net, const int32_t *sources, const int32_t *t
     if (n < 0) return fail(EAT_ERR_INVALID, "n must be >= 0");
     if (n == 0) return EAT_OK;
     if (!sources || !times || !arr_out) return fail(EAT_ERR_INVALID, "NULL query array");
+    for (const void *b : {(const void *)sources, (const void *)times, (const void *)arr_out,
+                          (const void *)workspace})
+        if (foreign_ptr(b, net->device)) return foreign_fail();
     DeviceGuard guard(net->device);
     cudaStream_t st = (cudaStream_t)stream;
     const bool d_src = is_device_ptr(sources), d_ts = is_device_ptr(times), d_out = is_device_ptr(arr_out);
@@ -1039,6 +1146,8 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
     if (n < 0) return fail(EAT_ERR_INVALID, "n must be >= 0");
     if (n == 0) return EAT_OK;
     if (!types || !times || !out) return fail(EAT_ERR_INVALID, "NULL argument");
+    for (const void *b : {(const void *)types, (const void *)times, (const void *)out})
+        if (foreign_ptr(b, net->device)) return foreign_fail();
     DeviceGuard guard(net->device);
     cudaError_t e = launch_next_departure(net->dev, types, times, n, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "next-departure kernel launch");
@@ -1170,6 +1279,7 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
     DeviceGuard guard(net->device);
     if (!is_device_ptr(sources) || !is_device_ptr(times))
         return fail(EAT_ERR_INVALID, "sample arrays must be device memory");
+    if (foreign_ptr(sources, net->device) || foreign_ptr(times, net->device)) return foreign_fail();
     cudaStream_t st = (cudaStream_t)stream;
     const eat_net *nets[1] = {net};
     std::vector<TuneCand> cands;
@@ -1190,6 +1300,7 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
     for (int b : {wide ? 1024 : 512, wide ? 512 : 1024, 256}) {
         for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, EAT_ORDER_AUTO, {}});
         cands.push_back({EAT_MODE_ASYNC, b, 8, EAT_ORDER_AUTO, {}});
+        for (int v : {8, 32}) cands.push_back({EAT_MODE_EDGE, b, v, EAT_ORDER_AUTO, {}});
     }
     cands.insert(cands.end(), pairs.begin(), pairs.end());
     size_t ws_need = 0;
@@ -1233,6 +1344,8 @@ extern "C" int eat_autotune_multi(const eat_net *const *nets, int32_t n_nets, co
     DeviceGuard guard(dev);
     if (!is_device_ptr(net_idx) || !is_device_ptr(sources) || !is_device_ptr(times))
         return fail(EAT_ERR_INVALID, "sample arrays must be device memory");
+    for (const void *b : {(const void *)net_idx, (const void *)sources, (const void *)times})
+        if (foreign_ptr(b, dev)) return foreign_fail();
     cudaStream_t st = (cudaStream_t)stream;
     // Output rows packed in query order: offsets from the sample's network indices.
     std::vector<int32_t> idx((size_t)n);
@@ -1265,6 +1378,7 @@ extern "C" int eat_autotune_multi(const eat_net *const *nets, int32_t n_nets, co
         for (int b : {512, 1024, 256}) {
             for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, ord, {}});
             cands.push_back({EAT_MODE_ASYNC, b, 8, ord, {}});
+            cands.push_back({EAT_MODE_EDGE, b, 8, ord, {}});
         }
     size_t ws_need = 0;
     int rc = usable_candidates(nets, n_nets, n, cands, ws_need);
@@ -1331,6 +1445,8 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     DeviceGuard guard(net->device);
     if (!is_device_ptr(sources) || !is_device_ptr(times) || !is_device_ptr(arr_out))
         return fail(EAT_ERR_INVALID, "sources, times and arr_out must be device memory");
+    for (const void *b : {(const void *)sources, (const void *)times, (const void *)arr_out})
+        if (foreign_ptr(b, net->device)) return foreign_fail();
     Plan p;
     int rc = make_plan(net->device, net->host.n_stops, n, 1, opts, p, -1, net, false);
     if (rc) return rc;

@@ -1,5 +1,5 @@
 // Host preprocessing: connections -> connection types -> clusters -> AP cover
-// (Section IV-A, graph representation and preprocessing algorithm).
+// (Section III-A, graph representation and preprocessing algorithm).
 //
 // Layout produced (see eat_net_view in eat.h):
 //   row_ptr[V+1]  types grouped by tail stop u, each group ordered by (v, lambda)
@@ -105,7 +105,7 @@ void build_chunk(Chunk &ch, const std::vector<int64_t> &u_off, std::vector<Rec> 
 
 namespace {
 
-// Greedy AP cover (Section II, Arithmetic Progression Technique): repeatedly take
+// Greedy AP cover (Section I-A, Arithmetic Progression Technique): repeatedly take
 // the smallest uncovered value a; among the APs a, a+d, a+2d, ... that stay inside
 // the set (one per later value, i.e. per difference d, each extended as far as it
 // goes) take the one covering the most uncovered values, then the longest, then
@@ -403,7 +403,7 @@ int build_host_csr(const eat_csr_input *in, int32_t width, int32_t t0, HostNet &
     return EAT_OK;
 }
 
-// Sub-trips (Section III-G).  A trip of k connections, ordered by departure, is cut
+// Sub-trips (Section II-G).  A trip of k connections, ordered by departure, is cut
 // into consecutive sub-trips of r connections (the last one shorter); r is the
 // nearest integer to sqrt(k) (EAT_SUBTRIPS_SQRT_K) or to the square root of the
 // mean trip length (EAT_SUBTRIPS_SQRT_MEAN), at least 2.  A sub-trip
@@ -496,7 +496,7 @@ int add_subtrips(const eat_connections *c, int32_t scheme, std::vector<int32_t> 
 // index and count of its further APs, the first departure of the next non-empty
 // cluster, and the type's head stop, duration and head row.  One load of the
 // entry answers getConnection for most clusters (Algorithm 6 inside the hourly
-// cluster of Section III-D) and gives everything Relax (Algorithm 3) and the
+// cluster of Section II-D) and gives everything Relax (Algorithm 3) and the
 // frontier push need.
 int build_fused(HostNet &h) {
     const int32_t T = h.n_types, W = h.width, t0 = h.t0;
@@ -520,14 +520,15 @@ int build_fused(HostNet &h) {
         int64_t extra = 0;   // each cluster's list padded to an even length (16-byte aligned)
         for (int32_t k = kf; k <= kl; ++k) {
             const int32_t n = h.cl[b + k + 1] - h.cl[b + k];
-            const int32_t m = std::max(0, n - 2) + (n >= kCountOverflow ? 2 : 0);   // + count header
+            const int32_t m = std::max(0, n - kInlineAps) + (n >= kCountOverflow ? 2 : 0);   // + count header
             extra += m + (m & 1);
         }
         xoff[t + 1] = xoff[t] + extra;
     }
     if (xoff[T] / 2 >= (int64_t)1 << 24)
-        return fail(EAT_ERR_INVALID, "more than 2^25 APs beyond the two inline per cluster");
+        return fail(EAT_ERR_INVALID, "more than 2^25 APs beyond the four inline per cluster");
     try {
+        h.tr.assign((size_t)T * 4, 0);
         h.ce.assign((size_t)T * (size_t)Y * 8, 0);
         h.apx.resize((size_t)xoff[T] * 2);
     } catch (const std::bad_alloc &) {
@@ -540,6 +541,11 @@ int build_fused(HostNet &h) {
             const int32_t kf = (h.type_rec[4 * (size_t)t + 2] - t0) / W;
             const int32_t kl = (h.type_rec[4 * (size_t)t + 3] - t0) / W;
             const int32_t b = h.type_cl[t];
+            int32_t *r = &h.tr[(size_t)t * 4];
+            r[0] = v;
+            r[1] = (int32_t)((uint32_t)lam | ((uint32_t)std::min(dv, kCountOverflow) << 24));
+            r[2] = vb;
+            r[3] = h.type_rec[4 * (size_t)t + 3];
             int64_t x = xoff[t];
             for (int32_t kr = 0; kr < Y; ++kr) {
                 int32_t *e = &h.ce[((size_t)kr * (size_t)T + (size_t)t) * 8];
@@ -550,15 +556,18 @@ int build_fused(HostNet &h) {
                     lo = h.cl[b + k];
                     n = h.cl[b + k + 1] - lo;
                 }
-                const uint32_t rel0 = n >= 1 ? (uint32_t)((int64_t)h.ap[2 * (size_t)lo] - cbase) : 0u;
-                const uint32_t rel1 = n >= 2 ? (uint32_t)((int64_t)h.ap[2 * (size_t)(lo + 1)] - cbase) : 0u;
-                e[0] = (int32_t)(rel0 | (rel1 << 16));
-                e[1] = n >= 1 ? (int32_t)h.ap[2 * (size_t)lo + 1] : 0;
-                e[2] = n >= 2 ? (int32_t)h.ap[2 * (size_t)(lo + 1) + 1] : 0;
+                // Inline AP j: start relative to the cluster (16 bits) and sc.
+                auto rel = [&](int32_t j) {
+                    return n > j ? (uint32_t)((int64_t)h.ap[2 * (size_t)(lo + j)] - cbase) : 0u;
+                };
+                auto sc = [&](int32_t j) { return n > j ? (int32_t)h.ap[2 * (size_t)(lo + j) + 1] : 0; };
+                e[0] = (int32_t)(rel(0) | (rel(1) << 16));
+                e[1] = sc(0);
+                e[2] = sc(1);
                 e[4] = (int32_t)(((uint32_t)(x / 2)) | ((uint32_t)std::min(n, kCountOverflow) << 24));
-                e[5] = v;
-                e[6] = (int32_t)((uint32_t)lam | ((uint32_t)std::min(dv, kCountOverflow) << 24));
-                e[7] = vb;
+                e[5] = (int32_t)(rel(2) | (rel(3) << 16));
+                e[6] = sc(2);
+                e[7] = sc(3);
                 int64_t m = 0;
                 if (n >= kCountOverflow) {     // count header: two slots, count in the first
                     h.apx[2 * (size_t)x] = (uint32_t)n;
@@ -568,7 +577,7 @@ int build_fused(HostNet &h) {
                     x += 2;
                     m += 2;
                 }
-                for (int32_t j = 2; j < n; ++j, ++x, ++m) {
+                for (int32_t j = kInlineAps; j < n; ++j, ++x, ++m) {
                     h.apx[2 * (size_t)x] = h.ap[2 * (size_t)(lo + j)];
                     h.apx[2 * (size_t)x + 1] = h.ap[2 * (size_t)(lo + j) + 1];
                 }

@@ -34,53 +34,66 @@ __device__ __forceinline__ int32_t ap_candidate(int32_t start, uint32_t sc, int3
 }
 
 // getConnectionFromAPs (Algorithm 6) over the APs of one cluster entry, with the
-// Cluster-AP fallback of Section III-D: if the cluster has no departure >= e, the
+// Cluster-AP fallback of Section II-D: if the cluster has no departure >= e, the
 // answer is the first departure of the next non-empty cluster (`next`).
-// a = {rel0 | rel1 << 16, sc0, sc1, next}; n APs, the third and later at apx[x..];
-// base is the cluster's start time.
-__device__ __forceinline__ int32_t cluster_lookup(const int4 a, int32_t n, int32_t x, int32_t base,
-                                                  int32_t e, const uint2 *__restrict__ apx,
-                                                  int32_t &aps) {
+// a = {rel0 | rel1 << 16, sc0, sc1, next}, b = {x/2 | n << 24, rel2 | rel3 << 16, sc2,
+// sc3}; n APs, the fifth and later at apx[x..]; base is the cluster's start time.
+// APs are ordered by first term, so the scan stops at the first start >= the best
+// candidate so far.
+__device__ __forceinline__ int32_t cluster_lookup(const int4 a, const int4 b, int32_t n, int32_t x,
+                                                  int32_t base, int32_t e,
+                                                  const uint2 *__restrict__ apx, int32_t &aps) {
     int32_t tc = kInf;
     if (n > 0) {
         ++aps;
         tc = ap_candidate(base + (a.x & 0xffff), (uint32_t)a.y, e);
-        const int32_t start1 = base + (int32_t)((uint32_t)a.x >> 16);
-        if (n > 1 && start1 < tc) {           // APs are ordered by first term
+        const int32_t s1 = base + (int32_t)((uint32_t)a.x >> 16);
+        if (n > 1 && s1 < tc) {
             ++aps;
-            tc = min(tc, ap_candidate(start1, (uint32_t)a.z, e));
-            // Further APs: batches of 8 loaded together (the list is 16-byte aligned
-            // and padded to an even length), so one L2 round trip covers a batch.
-            const int32_t m = n - 2;
-            const uint4 *p = reinterpret_cast<const uint4 *>(apx + x);
-            for (int32_t j = 0; j < m; j += 8) {
-                uint4 r[4];
+            tc = min(tc, ap_candidate(s1, (uint32_t)a.z, e));
+            const int32_t s2 = base + (b.y & 0xffff);
+            if (n > 2 && s2 < tc) {
+                ++aps;
+                tc = min(tc, ap_candidate(s2, (uint32_t)b.z, e));
+                const int32_t s3 = base + (int32_t)((uint32_t)b.y >> 16);
+                if (n > 3 && s3 < tc) {
+                    ++aps;
+                    tc = min(tc, ap_candidate(s3, (uint32_t)b.w, e));
+                    // Further APs: batches of 8 loaded together (the list is 16-byte
+                    // aligned and padded to an even length), one L2 round trip a batch.
+                    // A count of 255 means the true count heads the list in two slots.
+                    int32_t m = n - kInlineAps;
+                    const uint2 *lst = apx + x;
+                    if (n == kCountOverflow) {
+                        m = (int32_t)__ldg(lst).x - kInlineAps;
+                        lst += 2;
+                    }
+                    const uint4 *p = reinterpret_cast<const uint4 *>(lst);
+                    for (int32_t j = 0; j < m; j += 8) {
+                        uint4 r[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    r[q] = (j + 2 * q < m) ? __ldg(p + (j >> 1) + q) : make_uint4(0u, 0u, 0u, 0u);
+                        for (int q = 0; q < 4; ++q)
+                            r[q] = (j + 2 * q < m) ? __ldg(p + (j >> 1) + q) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (j + 2 * q < m) tc = min(tc, ap_candidate((int32_t)r[q].x, r[q].y, e));
-                    if (j + 2 * q + 1 < m) tc = min(tc, ap_candidate((int32_t)r[q].z, r[q].w, e));
+                        for (int q = 0; q < 4; ++q) {
+                            if (j + 2 * q < m) tc = min(tc, ap_candidate((int32_t)r[q].x, r[q].y, e));
+                            if (j + 2 * q + 1 < m) tc = min(tc, ap_candidate((int32_t)r[q].z, r[q].w, e));
+                        }
+                        aps += min(8, m - j);
+                        if (j + 8 < m && (int32_t)r[3].z >= tc) break;   // later starts are larger
+                    }
                 }
-                aps += min(8, m - j);
-                if (j + 8 < m && (int32_t)r[3].z >= tc) break;   // later starts are larger
             }
         }
     }
     return tc == kInf ? a.w : tc;
 }
 
-// Count and index of a cluster entry's APs (b = {x/2 | n << 24, ...}); a count of
-// 255 is read from the two-slot header that then starts the list.
-__device__ __forceinline__ void entry_aps(const int4 b, const uint2 *__restrict__ apx, int32_t &n,
-                                          int32_t &x) {
+// Count and index of a cluster entry's APs (b = {x/2 | n << 24, ...}); a count of 255
+// stands for 255 or more (cluster_lookup then reads the true count from the list).
+__device__ __forceinline__ void entry_aps(const int4 b, int32_t &n, int32_t &x) {
     n = (int32_t)((uint32_t)b.x >> 24);
     x = (b.x & 0xffffff) * 2;
-    if (n == kCountOverflow) {
-        n = (int32_t)__ldg(apx + x).x;
-        x += 2;
-    }
 }
 
 // Cluster slot of time e relative to the first stored cluster; e before the first
@@ -116,17 +129,23 @@ __device__ __forceinline__ void load_entry(const int4 *c, int4 &a, int4 &b) {
         : "l"(c));
 }
 
-// getConnection of type t at time e: least departure >= e, or kInf.
+// Cluster entry of type t for stored cluster slot k (cluster-major table).
+__device__ __forceinline__ const int4 *entry_at(const NetDev &N, int32_t k, int32_t t) {
+    return N.ce + 2 * ((int64_t)k * N.n_types + t);
+}
+
+// getConnection of type t at time e: least departure >= e, or kInf (none after the
+// type's last departure, kept in its type record).
 __device__ __forceinline__ int32_t next_departure(const NetDev &N, int32_t t, int32_t e,
                                                   int32_t &aps) {
+    if (e > __ldg(&N.tr[t].w)) return kInf;
     const int32_t k = cluster_slot(N, e);
     if (k >= N.y) return kInf;
-    const int4 *c = N.ce + 2 * ((int64_t)k * N.n_types + t);
     int4 a, b;
-    load_entry(c, a, b);
+    load_entry(entry_at(N, k, t), a, b);
     int32_t n, x;
-    entry_aps(b, N.apx, n, x);
-    return cluster_lookup(a, n, x, cluster_base(N, k), e, N.apx, aps);
+    entry_aps(b, n, x);
+    return cluster_lookup(a, b, n, x, cluster_base(N, k), e, N.apx, aps);
 }
 
 }  // namespace eat

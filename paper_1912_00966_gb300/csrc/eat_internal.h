@@ -18,26 +18,29 @@ namespace eat {
 // Device-side descriptor of one resident network (plain pointers into one blob).
 //
 // Device layout (derived from the logical arrays of HostNet by build_fused):
+//   tr[t]         16-byte record of connection type t: {v, lambda | d << 24, row_ptr[v],
+//                 last departure}: head stop, duration, types leaving v (255 = read
+//                 row_ptr), the head's first type, and the type's last departure
 //   ce[k*T + t]   32-byte entry of type t for cluster k_min + k, for every cluster
 //                 of the network (the paper's dense CL table, cluster-major so that
 //                 lookups at nearby times fall in one slab of T entries), read in
 //                 one load:
 //                   int4 {rel0 | rel1 << 16, sc0, sc1, next}
-//                   int4 {x/2 | n << 24, v, lambda | d << 24, row_ptr[v]}
-//                 the cluster's n APs: the first two inline with first terms
+//                   int4 {x/2 | n << 24, rel2 | rel3 << 16, sc2, sc3}
+//                 the cluster's n APs: the first four inline with first terms
 //                 base + rel (base = t0 + (k_min + k) * width) and
 //                 sc = (difference << 16) | terms, the others at apx[x ..] (x even);
 //                 n = 255 means more: the true count heads the list in two slots;
-//                 next = first departure of the next non-empty cluster (INF if none);
-//                 v, lambda: the type's head stop and duration; d: types leaving v
-//                 (255 = read row_ptr)
-//   apx[]         uint2 {first term, sc} of the third and later APs of a cluster
+//                 next = first departure of the next non-empty cluster (INF if none)
+//   apx[]         uint2 {first term, sc} of the fifth and later APs of a cluster
 //   row_ptr[V+1]  types leaving stop u are row_ptr[u] .. row_ptr[u+1]-1
 constexpr int32_t kCountOverflow = 255;
 constexpr int32_t kMaxDuration = 1 << 24;
+constexpr int32_t kInlineAps = 4;
 
 struct NetDev {
     const int32_t *row_ptr;   // [V + 1] types by tail stop
+    const int4 *tr;           // [T] type records
     const int4 *ce;           // [2 * y * T], cluster-major
     const uint2 *apx;         // [n_apx]
     int32_t n_stops;
@@ -68,6 +71,7 @@ struct HostNet {
     std::vector<uint32_t> ap;        // 2 n_ap
     // Device layout (see NetDev).
     int32_t k_min = 0, y = 1;
+    std::vector<int32_t> tr;         // 4 T
     std::vector<int32_t> ce;         // 8 T y
     std::vector<uint32_t> apx;       // 2 n_apx
 };
@@ -102,7 +106,7 @@ void clear_error();
 int build_host(const eat_connections *c, int32_t width, int32_t t0, HostNet &h);
 
 // Sub-trips (eat_build.cpp): the connections plus one artificial connection per
-// sub-trip of >= 2 connections (Section III-G), as new SoA arrays.
+// sub-trip of >= 2 connections (Section II-G), as new SoA arrays.
 int add_subtrips(const eat_connections *c, int32_t scheme, std::vector<int32_t> &u,
                  std::vector<int32_t> &v, std::vector<int32_t> &dep, std::vector<int32_t> &dur,
                  int64_t &n_added);

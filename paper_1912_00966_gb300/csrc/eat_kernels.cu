@@ -1,6 +1,6 @@
 // sm_103a kernels for earliest-arrival-time queries (Cluster-AP fixpoint).
 //
-// Per query (Algorithms 2-5 with the Cluster-AP lookup of Section III-D):
+// Per query (Algorithms 2-5 with the Cluster-AP lookup of Section II-D):
 //   init     e[] = INF, e[s] = t_s, frontier = {s}                 (Algorithm 2)
 //   round    for every stop u of the frontier and every connection type
 //            (u, v, lambda) leaving u: find the first departure t_c >= e[u]
@@ -8,10 +8,10 @@
 //            Algorithm 6), and if t_c + lambda < e[v] lower e[v] with atomicMin
 //            and put v on the next frontier                        (Algorithm 3)
 //   stop     when a round puts nobody on the next frontier.
-// The frontier replaces the paper's active[]/nextactive[] flags (Section IV-B):
+// The frontier replaces the paper's active[]/nextactive[] flags (Section III-B):
 // a stop joins the next frontier only after its e[] was lowered, through a
 // test-and-set on a per-round bitmap, so each stop appears at most once per
-// round; atomicMin resolves concurrent lowerings (Section IV-C).
+// round; atomicMin resolves concurrent lowerings (Section III-C).
 //
 // CTA mode: one thread block owns one query at a time (persistent blocks take
 // queries from an atomic counter), so rounds are separated by one block barrier
@@ -20,14 +20,17 @@
 // described at their kernels below.
 //
 // Work items: when a stop v joins the next frontier, the thread that lowered e[v]
-// writes one (v, type) item per connection type leaving v into shared memory, so
-// the next round hands every thread one (stop, type) pair: the paper's one thread
-// per connection type (Algorithm 5), restricted to the active tails.  Per item the
-// dependent memory chain is one L2 round trip: its 32-byte cluster entry (whose
-// address depends only on the type and e[u]'s cluster) carries the head stop,
-// duration and head row as well; e[u], e[v] and the frontier live in shared memory.
-// Stops whose items do not fit spill to a global queue and are expanded by
-// `vwarp`-lane sub-warps (Section III-F's virtual warps).
+// writes one (v, type) item per connection type leaving v into shared memory (one
+// 32- or 64-bit store each), so the next round hands every thread one (stop, type)
+// pair: the paper's one thread per connection type (Algorithm 5), restricted to the
+// active tails.  Per item, the type's 16-byte
+// record (head, duration, head row, last departure), e[u] and the 32-byte cluster
+// entry of e[u]'s cluster (whose address depends only on the type and the cluster;
+// two-word items carry the cluster at push time so that this load need not wait for
+// e[u]) are loaded together, then e[v] beside any further APs: two dependent global
+// round trips when arrivals live in global memory, one when they are in shared
+// memory.  Stops whose items do not fit spill to a global queue and are expanded by
+// `vwarp`-lane sub-warps (Section II-F's virtual warps).
 //
 // Buffers per query: arrivals in shared memory (ARR = kArrShared), in global
 // memory (kArrGlobal: the output row, or the block's scratch row when the output
@@ -64,7 +67,8 @@ __device__ __forceinline__ int32_t next_query(const QueryArgs &qa) {
 // device-side head below the host's tail, read with acquire semantics so that the
 // entry written before it is visible), copies its fields to s_ring and returns its
 // ring slot; it returns -1 when the host's stop flag is set and nothing is left, or
-// after rg.idle_iters polls without a request (every wait bounded).
+// after rg.idle_iters polls without a request (every wait bounded: polls 2 us apart
+// for the first 512, then 20 us apart).
 __device__ __forceinline__ int64_t ld_acquire_sys(const int64_t *p) {
     int64_t v;
     asm volatile("ld.acquire.sys.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -89,7 +93,7 @@ __device__ int32_t ring_next(const RingArgs &R, int32_t *s_ring) {
             h = was;
         }
         if (*(const volatile int32_t *)R.stop) return -1;
-        __nanosleep(2000);
+        __nanosleep(it < 512 ? 2000 : 20000);       // back off after about 1 ms idle
     }
     return -1;
 }
@@ -105,11 +109,6 @@ __device__ __forceinline__ void ring_done(const RingArgs &R, int32_t slot, int32
 constexpr int32_t kNullItem = -1;           // hole left by a stop that spilled
 constexpr int32_t kFirstItem = INT32_MIN;    // flag on the first item of a stop
 constexpr int32_t kNoSlot = 255;             // item tag: no cluster slot recorded
-
-// Cluster entry of type t for stored cluster slot k (cluster-major table).
-__device__ __forceinline__ const int4 *entry_at(const NetDev &N, int32_t k, int32_t t) {
-    return N.ce + 2 * ((int64_t)k * N.n_types + t);
-}
 
 // Items are (stop, type) pairs in two int32 arrays per buffer, or, with PACK (networks
 // of at most 32,767 stops and 65,535 types), one word per item: first-item flag << 31 |
@@ -192,10 +191,11 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
         int32_t c_vert = 0, c_types = 0, c_evals = 0, c_lookups = 0, c_aps = 0, c_relax = 0;
         while (n_items + n_spill > 0 && rounds < qa.max_rounds) {
             const int wr = rounds & 1, rd = wr ^ 1;
+            // One-word items (PACK) or two-word items {stop | first flag, type | tag}.
             int32_t *const iu_rd = item_base + (PACK ? rd : 2 * rd) * icap;
-            int32_t *const it_rd = iu_rd + icap;           // (unused with PACK)
             int32_t *const iu_wr = item_base + (PACK ? wr : 2 * wr) * icap;
-            int32_t *const it_wr = iu_wr + icap;
+            const int2 *const i2_rd = reinterpret_cast<const int2 *>(iu_rd);
+            int2 *const i2_wr = reinterpret_cast<int2 *>(iu_wr);
             const int32_t *const sp_rd = spill_base + (int64_t)rd * qa.vmax;
             int32_t *const sp_wr = spill_base + (int64_t)wr * qa.vmax;
             uint32_t *const pmask = wr ? mask1 : mask0;    // stops pushed this round
@@ -207,87 +207,130 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                 s_spill[nx] = 0;
             }
 
-            // Relax one type of tail u from its cluster entry (Algorithm 3 with
-            // getConnection, Algorithm 6); when t_c + lambda is below the e[v] read just
-            // before, lower e[v] with an atomic min whose result is not waited for and put
-            // v on the next frontier as items or as a spilled stop.  Every lowering is
-            // made by a thread whose candidate was below its read, so every lowering
-            // pushes v (at most once a round: the bitmap); a push whose min lost to a
-            // lower one made meanwhile only repeats work.
-            auto relax_entry = [&](int32_t e_u, int32_t k, const int4 ca, const int4 cb) {
-                ++c_types;
+            // Relaxation (Algorithm 3 with getConnection, Algorithm 6) in two steps.
+            // lookup: t_c + lambda of one type of tail u from its cluster entry and type
+            // record, for e[u] at or before the type's last departure (so that some
+            // departure is at or after e[u]).  lower: when that candidate is below the
+            // e[v] read beside the lookup, e[v] is lowered with an atomic min whose result
+            // is not waited for and v goes on the next frontier as items or as a spilled
+            // stop: every lowering is made by a thread whose candidate was below its read,
+            // so every lowering pushes v (at most once a round: the bitmap); a push whose
+            // min lost to a lower one made meanwhile only repeats work.  In EAT_MODE_EDGE
+            // a stop with at least vwarp types is queued whole for a vwarp-lane sub-warp
+            // (the mapping chosen by degree).
+            auto lookup = [&](int32_t e_u, int32_t k, const int4 ca, const int4 cb,
+                              const int4 tr) -> int32_t {  // tr = {v, lambda|d, row of v, last}
                 ++c_lookups;
-                int32_t n, x;                               // cb = {x|n, v, lambda|d, row of v}
-                entry_aps(cb, N.apx, n, x);
-                const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, k), e_u, N.apx, c_aps);
-                if (tc == kInf) return;                     // no departure left (Section IV-D)
                 ++c_evals;
-                const int32_t v = cb.y;
-                const int32_t cand = tc + (cb.z & 0xffffff);
-                if (cand >= load_arr(arr, v, arr_shared)) return;
+                int32_t n, x;
+                entry_aps(cb, n, x);
+                return cluster_lookup(ca, cb, n, x, cluster_base(N, k), e_u, N.apx, c_aps) +
+                       (tr.y & 0xffffff);
+            };
+            auto lower = [&](const int4 tr, int32_t cand, int32_t ev) {
+                if (cand >= ev) return;
+                const int32_t v = tr.x;
                 atomicMin(arr + v, cand);
                 ++c_relax;
-                int32_t d = (int32_t)((uint32_t)cb.z >> 24);  // types leaving v
-                if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - cb.w;
-                const int4 ty = make_int4(v, 0, cb.w, cb.w + d);
+                int32_t d = (int32_t)((uint32_t)tr.y >> 24);  // types leaving v
+                if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - tr.z;
                 if (d <= 0) return;
                 const uint32_t bit = 1u << (v & 31);
                 if (atomicOr(pmask + (v >> 5), bit) & bit) return;   // already queued
-                const int32_t base = atomicAdd(&s_items[cs], d);
-                if (base + d <= icap) {
-                    if (PACK) {
-                        const int32_t hv = (v << 16) | ty.z;
-                        iu_wr[base] = hv | kFirstItem;
-                        for (int32_t j = 1; j < d; ++j) iu_wr[base + j] = hv + j;
-                    } else {
-                        // The cluster slot of v's arrival now, for next round's entry load.
-                        int32_t tag = 0;
-                        if (qa.spec) {
-                            const int32_t kv = cluster_slot(N, cand);
-                            tag = (int32_t)((uint32_t)(kv < N.y ? kv : kNoSlot) << 24);
-                        }
-                        iu_wr[base] = v | kFirstItem;
-                        it_wr[base] = ty.z | tag;
-                        for (int32_t j = 1; j < d; ++j) {
-                            iu_wr[base + j] = v;
-                            it_wr[base + j] = (ty.z + j) | tag;
-                        }
-                    }
-                } else {
-                    for (int32_t j = base; j < icap; ++j) iu_wr[j] = kNullItem;
+                if (qa.edge && d >= vw) {                   // a sub-warp expands v whole
                     sp_wr[atomicAdd(&s_spill[cs], 1)] = v;
+                    return;
+                }
+                const int32_t base = atomicAdd(&s_items[cs], d);
+                if (base + d > icap) {
+                    for (int32_t j = base; j < icap; ++j) {
+                        if (PACK) iu_wr[j] = kNullItem;
+                        else i2_wr[j].x = kNullItem;
+                    }
+                    sp_wr[atomicAdd(&s_spill[cs], 1)] = v;
+                    return;
+                }
+                if (PACK) {
+                    const int32_t hv = (v << 16) | tr.z;
+                    iu_wr[base] = hv | kFirstItem;
+                    for (int32_t j = 1; j < d; ++j) iu_wr[base + j] = hv + j;
+                } else {
+                    // The cluster slot of v's arrival now, for next round's entry load.
+                    int32_t tag = 0;
+                    if (qa.spec) {
+                        const int32_t kv = cluster_slot(N, cand);
+                        tag = (int32_t)((uint32_t)(kv < N.y ? kv : kNoSlot) << 24);
+                    }
+                    i2_wr[base] = make_int2(v | kFirstItem, tr.z | tag);
+                    for (int32_t j = 1; j < d; ++j) i2_wr[base + j] = make_int2(v, (tr.z + j) | tag);
                 }
             };
-
-            // One thread per (stop, type) item.  Two-word items tagged with a cluster
-            // slot load that slot's entry at once, beside e[u], and load again only
-            // when e[u] has since moved to another cluster.
-            for (int32_t i = tid; i < n_items; i += nthr) {
-                const int32_t raw = iu_rd[i];
-                if (raw == kNullItem) continue;
-                const int32_t u = PACK ? (raw >> 16) & 0x7fff : raw & 0x7fffffff;
-                if (raw < 0) {                              // first item of u
-                    atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
-                    ++c_vert;
-                }
-                int32_t t, ks = kNoSlot;
+            // Item i: its stop u and type t (clearing u's bit in last round's bitmap at
+            // u's first item); loads the type record, e[u] and the cluster entry together:
+            // two-word items tagged with a cluster slot load that slot's entry at once and
+            // load again only when e[u] has since moved to another cluster; others load the
+            // entry of e[u]'s cluster as soon as e[u] is known.  Returns whether the type
+            // has a departure at or after e[u] (else it stops here, Section III-D).
+            auto load_item = [&](int32_t i, int32_t &e_u, int32_t &k, int4 &ca, int4 &cb,
+                                 int4 &tr) -> bool {
+                int32_t u, t, ks = kNoSlot;
                 if (PACK) {
+                    const int32_t raw = iu_rd[i];
+                    if (raw == kNullItem) return false;
+                    u = (raw >> 16) & 0x7fff;
                     t = raw & 0xffff;
+                    if (raw < 0) {
+                        atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
+                        ++c_vert;
+                    }
                 } else {
-                    const int32_t w = it_rd[i];
-                    t = qa.spec ? w & 0xffffff : w;
-                    if (qa.spec) ks = (int32_t)((uint32_t)w >> 24);
+                    const int2 it = i2_rd[i];
+                    if (it.x == kNullItem) return false;
+                    u = it.x & 0x7fffffff;
+                    t = qa.spec ? it.y & 0xffffff : it.y;
+                    if (qa.spec) ks = (int32_t)((uint32_t)it.y >> 24);
+                    if (it.x < 0) {
+                        atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
+                        ++c_vert;
+                    }
                 }
-                int4 ca, cb;
+                ++c_types;
                 if (!PACK && ks != kNoSlot) load_entry(entry_at(N, ks, t), ca, cb);
-                const int32_t e_u = load_arr(arr, u, arr_shared);
-                const int32_t k = cluster_slot(N, e_u);
-                if (k >= N.y) {                             // no departure left anywhere
-                    ++c_types;
-                    continue;
+                tr = __ldg(N.tr + t);
+                e_u = load_arr(arr, u, arr_shared);
+                k = cluster_slot(N, e_u);
+                if ((PACK || k != ks) && k < N.y) load_entry(entry_at(N, k, t), ca, cb);
+                return e_u <= tr.w;
+            };
+
+            if (!qa.edge) {
+                // One thread per (stop, type) item.
+                for (int32_t i = tid; i < n_items; i += nthr) {
+                    int32_t e_u, k;
+                    int4 ca = make_int4(0, 0, 0, 0), cb = ca, tr;
+                    if (!load_item(i, e_u, k, ca, cb, tr)) continue;
+                    const int32_t ev = load_arr(arr, tr.x, arr_shared);
+                    lower(tr, lookup(e_u, k, ca, cb, tr), ev);
                 }
-                if (PACK || k != ks) load_entry(entry_at(N, k, t), ca, cb);
-                relax_entry(e_u, k, ca, cb);
+            } else {
+                // EAT_MODE_EDGE: a warp's lanes take consecutive items and every lane runs
+                // every pass (lanes past the end carry none); lanes whose types share a head
+                // stop v (the types of one edge, or of edges into one stop) reduce their
+                // candidates with a warp min, and one lane per head stop lowers e[v].
+                for (int32_t ib = tid & ~31; ib < n_items; ib += nthr) {
+                    const int32_t i = ib + (tid & 31);
+                    int32_t e_u = 0, k = 0, ev = kInf, cand = kInf;
+                    int4 ca = make_int4(0, 0, 0, 0), cb = ca, tr = ca;
+                    bool live = i < n_items && load_item(i, e_u, k, ca, cb, tr);
+                    if (live) {
+                        ev = load_arr(arr, tr.x, arr_shared);
+                        cand = lookup(e_u, k, ca, cb, tr);
+                    }
+                    const unsigned grp = __match_any_sync(0xffffffffu, live ? tr.x : -1 - (tid & 31));
+                    const int32_t m = __reduce_min_sync(grp, cand);
+                    const unsigned first = __ballot_sync(0xffffffffu, cand == m) & grp;
+                    if (live && (tid & 31) == __ffs(first) - 1) lower(tr, cand, ev);
+                }
             }
             // Spilled stops: `vw` lanes per stop stride over its types.
             for (int32_t i = sub; i < n_spill; i += nsub) {
@@ -300,14 +343,18 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                 }
                 const int32_t e_u = load_arr(arr, u, arr_shared);
                 const int32_t k = cluster_slot(N, e_u);
-                if (k >= N.y) {
+                if (k >= N.y) {                             // no departure left anywhere
                     if (lane == 0) c_types += end - beg;
                     continue;
                 }
                 for (int32_t t = beg + lane; t < end; t += vw) {
+                    ++c_types;
                     int4 ca, cb;
                     load_entry(entry_at(N, k, t), ca, cb);
-                    relax_entry(e_u, k, ca, cb);
+                    const int4 tr = __ldg(N.tr + t);
+                    if (e_u > tr.w) continue;
+                    const int32_t ev = load_arr(arr, tr.x, arr_shared);
+                    lower(tr, lookup(e_u, k, ca, cb, tr), ev);
                 }
             }
             __syncthreads();
@@ -530,28 +577,31 @@ eat_pair_kernel(const __grid_constant__ NetTable<1> nets, const QueryArgs qa) {
         }
 
         // Relax type t of tail u for slot j (Algorithm 3 with Algorithm 6).
+        // Relax type t of tail u for slot j (Algorithm 3 with Algorithm 6): entry and type
+        // record loaded together, e[v] read beside the further APs, as in eat_cta_kernel.
         auto relax = [&](int j, int32_t e_u, int32_t k, int32_t t) {
-            const int4 *c = N.ce + 2 * ((int64_t)k * N.n_types + t);
-            int4 ca, cb;
-            load_entry(c, ca, cb);
+            int4 ca = make_int4(0, 0, 0, 0), cb = ca;
+            if (k < N.y) load_entry(entry_at(N, k, t), ca, cb);
+            const int4 tr = __ldg(N.tr + t);             // {v, lambda|d, row of v, last}
+            if (COUNT) pc.add(j, 1, 1);
+            if (e_u > tr.w) return;                      // no departure left (Section III-D)
+            int32_t *const a = smem + j * vpad;
+            const int32_t v = tr.x;
+            const int32_t ev = load_arr(a, v, true);
             int32_t n, x, aps = 0;
-            entry_aps(cb, N.apx, n, x);
-            const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, k), e_u, N.apx, aps);
+            entry_aps(cb, n, x);
+            const int32_t tc = cluster_lookup(ca, cb, n, x, cluster_base(N, k), e_u, N.apx, aps);
             if (COUNT) {
-                pc.add(j, 1, 1);
+                pc.add(j, 2, 1);
                 pc.add(j, 3, 1);
                 pc.add(j, 4, aps);
             }
-            if (tc == kInf) return;
-            if (COUNT) pc.add(j, 2, 1);
-            int32_t *const a = smem + j * vpad;
-            const int32_t v = cb.y;
-            const int32_t cand = tc + (cb.z & 0xffffff);
-            if (cand >= load_arr(a, v, true)) return;
+            const int32_t cand = tc + (tr.y & 0xffffff);
+            if (cand >= ev) return;
             atomicMin(a + v, cand);                        // result not waited for, as above
             if (COUNT) pc.add(j, 5, 1);
-            int32_t d = (int32_t)((uint32_t)cb.z >> 24);
-            if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - cb.w;
+            int32_t d = (int32_t)((uint32_t)tr.y >> 24);
+            if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - tr.z;
             if (d <= 0) return;
             uint32_t *const pmask = masks + (j * 2 + wr) * qa.mask_words;
             const uint32_t bit = 1u << (v & 31);
@@ -560,7 +610,7 @@ eat_pair_kernel(const __grid_constant__ NetTable<1> nets, const QueryArgs qa) {
             const uint32_t lo = before & 0xffffu, hi = before >> 16;
             if (lo + hi + (uint32_t)d <= (uint32_t)icap) {
                 const int32_t pos = j ? icap - (int32_t)hi - d : (int32_t)lo;
-                const int32_t hv = (v << 16) | cb.w;
+                const int32_t hv = (v << 16) | tr.z;
                 it_wr[pos] = hv | kFirstItem;
                 for (int32_t jj = 1; jj < d; ++jj) it_wr[pos + jj] = hv + jj;
             } else {
@@ -581,12 +631,7 @@ eat_pair_kernel(const __grid_constant__ NetTable<1> nets, const QueryArgs qa) {
                 if (COUNT) pc.add(j, 0, 1);
             }
             const int32_t e_u = load_arr(smem + j * vpad, u, true);
-            const int32_t k = cluster_slot(N, e_u);
-            if (k >= N.y) {
-                if (COUNT) pc.add(j, 1, 1);
-                continue;
-            }
-            relax(j, e_u, k, raw & 0xffff);
+            relax(j, e_u, cluster_slot(N, e_u), raw & 0xffff);
         }
         // Spilled stops of both slots: `vw` lanes per stop.
         const int32_t s0 = ns[0], sall = ns[0] + ns[1];
@@ -632,7 +677,7 @@ eat_pair_kernel(const __grid_constant__ NetTable<1> nets, const QueryArgs qa) {
 // lane), every lane claims one pending stop (clears its bit, then reads e[u]), the
 // warp spreads the claimed stops' (stop, type) pairs over its lanes and relaxes
 // them; a lowered e[v] sets v's bit after the atomicMin, so a stop improved after
-// it was read is claimed again (the invariant of Section IV-B's double buffer,
+// it was read is claimed again (the invariant of Section III-B's double buffer,
 // without the round barrier).  A work counter holds pending + claimed stops:
 // a producer adds one before publishing a bit, a claimed stop is subtracted only
 // after all its pushes, so the counter reaches zero exactly when no work is left.
@@ -770,22 +815,23 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
                 const int32_t t = st_beg[lo] + (j - st_pre[lo]);
                 const int32_t eu = st_e[lo], kk = st_k[lo];
                 ++c_types;
+                int4 ca, cb;
+                load_entry(entry_at(N, kk, t), ca, cb);
+                const int4 tr = __ldg(N.tr + t);             // {v, lambda|d, row of v, last}
+                if (eu > tr.w) continue;                     // no departure left
                 ++c_lookups;
-                const int4 *c = N.ce + 2 * ((int64_t)kk * N.n_types + t);
-                int4 ca, cb;                                 // cb = {x|n, v, lambda|d, row of v}
-                load_entry(c, ca, cb);
-                int32_t n, x;
-                entry_aps(cb, N.apx, n, x);
-                const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, kk), eu, N.apx, c_aps);
-                if (tc == kInf) continue;
                 ++c_evals;
-                const int32_t v = cb.y;
-                const int32_t cand = tc + (cb.z & 0xffffff);
-                if (cand >= load_arr(arr, v, arr_shared)) continue;
+                const int32_t v = tr.x;
+                const int32_t ev = load_arr(arr, v, arr_shared);
+                int32_t n, x;
+                entry_aps(cb, n, x);
+                const int32_t tc = cluster_lookup(ca, cb, n, x, cluster_base(N, kk), eu, N.apx, c_aps);
+                const int32_t cand = tc + (tr.y & 0xffffff);
+                if (cand >= ev) continue;
                 const int32_t old = atomicMin(arr + v, cand);
                 if (cand >= old) continue;
                 ++c_relax;
-                if (((uint32_t)cb.z >> 24) == 0) continue;  // v has no outgoing types
+                if (((uint32_t)tr.y >> 24) == 0) continue;  // v has no outgoing types
                 const uint32_t bit = 1u << (v & 31);
                 atomicAdd(&s_work, 1);                      // count before publishing
                 __threadfence_block();
@@ -999,23 +1045,24 @@ eat_cluster_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs 
         // success v joins this block's next frontier as items or as a spilled stop.
         auto relax = [&](int32_t e_u, int32_t k, int32_t t) {
             ++c_types;
+            int4 ca, cb;
+            load_entry(entry_at(N, k, t), ca, cb);
+            const int4 tr = __ldg(N.tr + t);             // {v, lambda|d, row of v, last}
+            if (e_u > tr.w) return;                      // no departure left (Section III-D)
             ++c_lookups;
-            int4 ca, cb;                                // cb = {x|n, v, lambda|d, row of v}
-            load_entry(N.ce + 2 * ((int64_t)k * N.n_types + t), ca, cb);
-            int32_t n, x;
-            entry_aps(cb, N.apx, n, x);
-            const int32_t tc = cluster_lookup(ca, n, x, cluster_base(N, k), e_u, N.apx, c_aps);
-            if (tc == kInf) return;                     // no departure left (Section IV-D)
             ++c_evals;
-            const int32_t v = cb.y;
-            const int32_t cand = tc + (cb.z & 0xffffff);
+            int32_t n, x;
+            entry_aps(cb, n, x);
+            const int32_t tc = cluster_lookup(ca, cb, n, x, cluster_base(N, k), e_u, N.apx, c_aps);
+            const int32_t v = tr.x;
+            const int32_t cand = tc + (tr.y & 0xffffff);
             int32_t *const ev = arr_of(v);
             if (cand >= *(volatile int32_t *)ev) return;
             const int32_t old = atomicMin(ev, cand);
             if (cand >= old) return;
             ++c_relax;
-            const int32_t row = cb.w;
-            int32_t d = (int32_t)((uint32_t)cb.z >> 24);  // types leaving v
+            const int32_t row = tr.z;
+            int32_t d = (int32_t)((uint32_t)tr.y >> 24);  // types leaving v
             if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - row;
             if (d <= 0) return;
             const uint32_t bit = bit_of(v);

@@ -1,10 +1,10 @@
-// Topology-driven variants of Section III (A to F), the paper's own execution
+// Topology-driven variants of Section II (A to F), the paper's own execution
 // model: one query at a time, every round one kernel over all connections, types
 // or edges, host-driven rounds with a flag read every `flag_every` rounds
-// (Section V-D).  Kept as a baseline for the frontier-driven kernels of
+// (Section IV-C).  Kept as a baseline for the frontier-driven kernels of
 // eat_kernels.cu and to show what each pruning step buys.
 //
-// Active stops (Section IV-B's active / nextactive pair) are two arrays of round
+// Active stops (Section III-B's active / nextactive pair) are two arrays of round
 // stamps: stop u is active in round i if stamp[i & 1][u] == i, and a stop lowered
 // in round i gets stamp[(i + 1) & 1][v] = i + 1, so neither array is ever
 // cleared.  `last` holds the latest round that lowered some arrival: after round
@@ -108,7 +108,7 @@ __global__ void ladder_type_kernel(LadderDev L, int32_t it_arg) {
     }
 }
 
-// Section III-C: one thread per type, getConnectionFromAPs (Algorithm 6) over the
+// Section II-C: one thread per type, getConnectionFromAPs (Algorithm 6) over the
 // type's whole-day AP tuples.
 __global__ void ladder_type_ap_kernel(LadderDev L, int32_t it_arg) {
     const int32_t it = round_of(L, it_arg);
@@ -134,15 +134,17 @@ __global__ void ladder_type_ap_kernel(LadderDev L, int32_t it_arg) {
 // Cluster-AP lookup of type t at e[u] and its relaxation.
 __device__ __forceinline__ void cluster_ap_relax(const LadderDev &L, const NetDev &N, int32_t t,
                                                  int32_t eu, int32_t k, int32_t it) {
+    const int4 tr = __ldg(N.tr + t);                     // {v, lambda|d, row of v, last}
+    if (eu > tr.w) return;                               // no departure left
     int4 a, b;
-    load_entry(N.ce + 2 * ((int64_t)k * N.n_types + t), a, b);
+    load_entry(entry_at(N, k, t), a, b);
     int32_t n, x, aps = 0;
-    entry_aps(b, N.apx, n, x);
-    const int32_t tc = cluster_lookup(a, n, x, cluster_base(N, k), eu, N.apx, aps);
-    if (tc != kInf) ladder_relax(L, b.y, tc + (b.z & 0xffffff), it);
+    entry_aps(b, n, x);
+    const int32_t tc = cluster_lookup(a, b, n, x, cluster_base(N, k), eu, N.apx, aps);
+    ladder_relax(L, tr.x, tc + (tr.y & 0xffffff), it);
 }
 
-// Section III-D: one thread per type, Cluster-AP lookup.
+// Section II-D: one thread per type, Cluster-AP lookup.
 __global__ void ladder_cluster_ap_kernel(LadderDev L, NetDev N, int32_t it_arg) {
     const int32_t it = round_of(L, it_arg);
     const int32_t stride = gridDim.x * blockDim.x;
@@ -155,7 +157,7 @@ __global__ void ladder_cluster_ap_kernel(LadderDev L, NetDev N, int32_t it_arg) 
     }
 }
 
-// Section III-E: one thread per edge, all its types by Cluster-AP.
+// Section II-E: one thread per edge, all its types by Cluster-AP.
 __global__ void ladder_edge_kernel(LadderDev L, NetDev N, int32_t it_arg) {
     const int32_t it = round_of(L, it_arg);
     const int32_t stride = gridDim.x * blockDim.x;
@@ -170,7 +172,7 @@ __global__ void ladder_edge_kernel(LadderDev L, NetDev N, int32_t it_arg) {
     }
 }
 
-// Section III-F: one warp per edge, the edge's types over the lanes.
+// Section II-F: one warp per edge, the edge's types over the lanes.
 __global__ void ladder_warp_kernel(LadderDev L, NetDev N, int32_t it_arg) {
     const int32_t it = round_of(L, it_arg);
     const int32_t lane = threadIdx.x & 31;

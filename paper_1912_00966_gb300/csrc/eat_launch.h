@@ -26,7 +26,8 @@ struct RingArgs {
     unsigned long long *head;    // requests claimed so far (device memory, CAS)
     int64_t row_stride;          // ints per result row of the pool at arr_out
     int32_t mask;                // ring capacity - 1 (a power of two)
-    int32_t idle_iters;          // polls (about 2 us apart) before an idle block leaves
+    int32_t idle_iters;          // polls (2 us apart, 20 us after the first 512) before an
+                                 // idle block leaves
 };
 
 struct QueryArgs {
@@ -61,6 +62,8 @@ struct QueryArgs {
                                // at push time (type | slot << 24): every network of the
                                // launch has < 2^24 types and <= 255 cluster slots
     RingArgs rg;               // ring mode only
+    int32_t edge;              // EAT_MODE_EDGE: warp min per head stop, stops with >= vwarp
+                               // types expanded whole by a sub-warp
 };
 
 // mem: 0 = arrivals and bitmaps in shared memory, 1 = arrivals global / bitmaps
@@ -94,6 +97,22 @@ cudaError_t launch_cluster(const NetDev &net, const QueryArgs &qa, int cluster, 
 const void *pair_kernel(bool count = false);
 cudaError_t launch_pair(const NetDev &net, const QueryArgs &qa, int grid, int block, size_t smem,
                         cudaStream_t st);
+// Serving ring (eat_server.cu): launch shape of the ring kernel for these networks,
+// and its launch with the caller's buffers.
+struct RingLaunch {
+    int mem = 0, block = 0, grid = 0;
+    size_t smem = 0;
+    size_t ws_bytes = 0;          // device workspace (spill queues of every block)
+    size_t rows_bytes = 0;        // device rows for arrivals kept out of shared memory
+    int64_t rows_stride = 0;      // ints per such row
+    int32_t vmax = 0;
+    int32_t vw_log2 = 3, qcap = 0, mask_words = 0, smem_mask_off = 0, smem_q_off = 0;
+    int32_t smem_arr_cap = 0;
+    int64_t spill_stride = 0;
+};
+int ring_setup(const eat_net *const *nets, int n_nets, RingLaunch &rl);
+int ring_launch(const eat_net *const *nets, int n_nets, const RingLaunch &rl, void *ws,
+                int32_t *arr_rows, int32_t *pool, const RingArgs &rg, cudaStream_t st);
 // order[0..n) = query indices sorted by t_s (15-minute buckets, earliest first; one
 // block, counting sort; the order inside a bucket is not fixed).
 cudaError_t launch_order(const int32_t *ts, int32_t n, int32_t *order, cudaStream_t st);

@@ -19,9 +19,11 @@ EAT_INF = 2**31 - 1
 EAT_OK, EAT_ERR_INVALID, EAT_ERR_OOM, EAT_ERR_CUDA = 0, 1, 2, 3
 EAT_ERR_NO_CONVERGENCE, EAT_ERR_NO_DEVICE, EAT_ERR_WORKSPACE = 4, 5, 6
 EAT_MODE_AUTO, EAT_MODE_CTA, EAT_MODE_CLUSTER, EAT_MODE_ASYNC, EAT_MODE_PAIR = 0, 1, 2, 3, 4
+EAT_MODE_EDGE = 5
 EAT_ORDER_AUTO, EAT_ORDER_BY_TIME, EAT_ORDER_AS_GIVEN = 0, 1, 2
 EAT_PLACE_AUTO, EAT_PLACE_SHARED, EAT_PLACE_GLOBAL_ARR, EAT_PLACE_GLOBAL = 0, 1, 2, 3
 EAT_SUBTRIPS_NONE, EAT_SUBTRIPS_SQRT_K, EAT_SUBTRIPS_SQRT_MEAN = 0, 1, 2
+EAT_ADMIT_RING, EAT_ADMIT_BATCH = 0, 1
 EAT_MAX_NETS = 128
 EAT_VAR_CONNECTION, EAT_VAR_TYPE, EAT_VAR_TYPE_AP = 1, 2, 3
 EAT_VAR_CLUSTER_AP, EAT_VAR_EDGE, EAT_VAR_WARP = 4, 5, 6
@@ -66,7 +68,7 @@ class eat_stats(ctypes.Structure):
 
 class eat_net_view(ctypes.Structure):
     _fields_ = [("row_ptr", _vp), ("type_rec", _vp), ("type_cl", _vp), ("cl", _vp),
-                ("ap", _vp), ("cluster_entries", _vp), ("ap_extra", _vp)]
+                ("ap", _vp), ("cluster_entries", _vp), ("ap_extra", _vp), ("type_records", _vp)]
 
 
 class eat_counters(ctypes.Structure):
@@ -89,7 +91,7 @@ class eat_query_opts(ctypes.Structure):
 
 class eat_server_opts(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
-                ("batch_wait_us", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("batch_wait_us", ctypes.c_int32), ("admission", ctypes.c_int32),
                 ("mem_budget", ctypes.c_int64)]
 
 
@@ -101,7 +103,8 @@ class eat_server_result(ctypes.Structure):
 class eat_server_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in (
         "submitted", "completed", "pending", "batches", "batched_queries", "max_batch_seen",
-        "max_inflight_seen", "max_pending_seen", "slots", "slot_bytes", "last_error")]
+        "max_inflight_seen", "max_pending_seen", "slots", "slot_bytes", "last_error",
+        "admitted_running", "base_bytes")]
 
 
 def _sig(name, res, args):
@@ -308,6 +311,7 @@ def eat_net_host_view(net: Net) -> dict:
         "cluster_entries": arr(view.cluster_entries, 8 * T * st["y"], np.int32)
         .reshape(st["y"], T, 8).transpose(1, 0, 2).copy(),
         "ap_extra": arr(view.ap_extra, 2 * st["n_ap_extra"], np.uint32).reshape(-1, 2),
+        "type_records": arr(view.type_records, 4 * T, np.int32).reshape(T, 4),
     }
 
 
@@ -427,12 +431,14 @@ def eat_last_error() -> str:
 
 
 class Server:
-    """Continuous-batching request loop over resident networks (eat_server_* in eat.h)."""
+    """Continuous-batching request loop over resident networks (eat_server_* in eat.h);
+    admission EAT_ADMIT_RING (default) or EAT_ADMIT_BATCH."""
 
-    def __init__(self, nets, max_batch=0, max_inflight=0, batch_wait_us=0, mem_budget=0):
+    def __init__(self, nets, max_batch=0, max_inflight=0, batch_wait_us=0, mem_budget=0,
+                 admission=0):
         self._nets = list(nets)
         arr = (_vp * len(self._nets))(*[x.handle.value for x in self._nets])
-        o = eat_server_opts(int(max_batch), int(max_inflight), int(batch_wait_us), 0,
+        o = eat_server_opts(int(max_batch), int(max_inflight), int(batch_wait_us), int(admission),
                             int(mem_budget))
         h = _vp()
         _check(_lib.eat_server_create(arr, len(self._nets), ctypes.byref(o), ctypes.byref(h)),

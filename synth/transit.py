@@ -1,12 +1,12 @@
 """Seeded synthetic transit timetables shaped like the paper's GTFS workloads.
 
-The paper measures on nine GTFS city feeds (Section V, Table I).  Those feeds are
+The paper measures on nine GTFS city feeds (Section IV, Table I).  Those feeds are
 not available here, so these generators stand in for them: stops on a grid or a
 random geometric graph, routes as random walks over that graph, trips that run
 every h seconds along a route, and one connection (u, v, t, lambda) per trip and
-route edge (Section II, Preliminaries: a connection leaves u at t and reaches v
+route edge (Section I-A, Preliminaries: a connection leaves u at t and reaches v
 at t + lambda).  Times are int32 seconds from 00:00 of the service day and may
-run past 24 h (Section V: some feeds cover more than a day).
+run past 24 h (Section IV: some feeds cover more than a day).
 
 This module only draws inputs.  It holds no part of the earliest-arrival
 computation and is shared, unchanged, by the oracle side and the CUDA side.

@@ -1,12 +1,12 @@
 """Pins of the oracle's arithmetic-progression cover and cluster split (no GPU).
 
 * the worked examples printed in the paper (tests/golden/ap_worked_examples.txt),
-* expansion of the cover == the input set (Section III-C: no extra departures),
+* expansion of the cover == the input set (Section II-C: no extra departures),
 * every greedy step takes an AP that, among all APs from the smallest uncovered
   number inside the set, covers the most uncovered numbers (checked by brute
   force enumeration, independent of the oracle's loop),
 * getConnection's plain definition against a sorted-list bisection, and the
-  cluster split against the hour arithmetic of Section III-D.
+  cluster split against the hour arithmetic of Section II-D.
 """
 import bisect
 import os

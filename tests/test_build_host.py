@@ -1,8 +1,8 @@
-"""libeat's host preprocessing (Section IV-A layout) against the oracle's definitions (no GPU).
+"""libeat's host preprocessing (Section III-A layout) against the oracle's definitions (no GPU).
 
 A host-only build (device = -1) exposes the built arrays; they must encode exactly
-the oracle's connection types (Section III-B), cluster split (Section III-D) and
-greedy AP cover (Section II), and the builder must reject invalid input.
+the oracle's connection types (Section II-B), cluster split (Section II-D) and
+greedy AP cover (Section I-A), and the builder must reject invalid input.
 """
 import numpy as np
 import pytest
@@ -89,7 +89,7 @@ def test_duplicates_merged_and_stats():
 
 
 def test_paper_worked_example_through_builder():
-    # Section III-C: departures 8:00, 8:15, ..., 18:00 on one type are a single AP
+    # Section II-C: departures 8:00, 8:15, ..., 18:00 on one type are a single AP
     # (8:00, 18:00, 15 min) when no cluster boundary cuts them.
     deps = np.arange(28800, 64801, 900, dtype=np.int32)
     n = deps.shape[0]
@@ -152,14 +152,17 @@ def test_empty_timetable_and_host_only_queries():
 ])
 def test_device_cluster_entries_match_oracle(make, width, t0):
     """Every (type, cluster) entry of the device layout holds exactly the oracle's greedy
-    cover of that cluster (first two APs inline, the rest in ap_extra, in order) and the
-    first departure of the next non-empty cluster (INF if none)."""
+    cover of that cluster (first four APs inline, the rest in ap_extra, in order) and the
+    first departure of the next non-empty cluster (INF if none); every type record holds
+    the type's head, duration, the head's out-degree and first type, and the type's last
+    departure."""
     tt = make()
     net = _build(tt, cluster_width=width, t0=t0)
     hv, st = eat.eat_net_host_view(net), eat.eat_get_stats(net)
     W = width or 3600
     types = oracle.connection_types(tt)
-    rp, rec, ce, apx = (hv[k] for k in ("row_ptr", "type_rec", "cluster_entries", "ap_extra"))
+    rp, rec, ce, apx, tr = (hv[k] for k in ("row_ptr", "type_rec", "cluster_entries", "ap_extra",
+                                            "type_records"))
     y, kmin = st["y"], st["k_min"]
     all_k = [(d - t0) // W for ds in types.values() for d in ds]
     assert kmin == min(all_k) and y == max(all_k) - kmin + 1
@@ -172,6 +175,9 @@ def test_device_cluster_entries_match_oracle(make, width, t0):
         for t in range(rp[u], rp[u + 1]):
             v, lam = int(rec[t][0]), int(rec[t][1])
             deps = types[(u, v, lam)]
+            r = [int(x_) & 0xFFFFFFFF for x_ in tr[t]]
+            assert (r[0], r[1] & 0xFFFFFF, r[2], r[3]) == (v, lam, rp[v], deps[-1])
+            assert r[1] >> 24 == min(255, rp[v + 1] - rp[v])
             clusters = oracle.cluster_sets(deps, width=W, t0=t0)
             for kr in range(y):
                 k = kmin + kr
@@ -180,16 +186,11 @@ def test_device_cluster_entries_match_oracle(make, width, t0):
                 n, x = e[4] >> 24, (e[4] & 0xFFFFFF) * 2
                 if n == 255:
                     n, x = int(apx[x][0]), x + 2
-                d = e[6] >> 24
-                assert (e[5], e[6] & 0xFFFFFF, e[7]) == (v, lam, rp[v])
-                assert d == min(255, rp[v + 1] - rp[v])
-                got = []
-                if n >= 1:
-                    got.append(dec(base + (e[0] & 0xFFFF), e[1]))
-                if n >= 2:
-                    got.append(dec(base + (e[0] >> 16), e[2]))
-                for j in range(2, n):
-                    got.append(dec(apx[x + j - 2][0], int(apx[x + j - 2][1])))
+                inline = [(e[0] & 0xFFFF, e[1]), (e[0] >> 16, e[2]), (e[5] & 0xFFFF, e[6]),
+                          (e[5] >> 16, e[7])]
+                got = [dec(base + rel, sc) for rel, sc in inline[:n]]
+                for j in range(4, n):
+                    got.append(dec(apx[x + j - 4][0], int(apx[x + j - 4][1])))
                 assert got == ap_cover(clusters.get(k, []))
                 later = [dd for dd in deps if (dd - t0) // W > k]
                 assert e[3] == (min(later) if later else INF)
@@ -220,7 +221,7 @@ def test_long_duration_rejected():
     assert "2^24" in str(ei.value)
 
 
-# ------------------------------------------------------------------ sub-trips (Section III-G)
+# ------------------------------------------------------------------ sub-trips (Section II-G)
 
 def _expand_connections(net):
     """All connections (u, v, t, lambda) encoded by a built network, from its host view."""
@@ -286,7 +287,7 @@ def test_subtrips_reject_broken_trips_and_missing_ids():
 
 @pytest.mark.parametrize("scheme", [1, 2])
 def test_subtrips_leave_earliest_arrivals_unchanged(scheme):
-    """Section III-G: the artificial connections ride the same vehicle, so the earliest
+    """Section II-G: the artificial connections ride the same vehicle, so the earliest
     arrival times of the enhanced timetable equal the original's (oracle on both)."""
     tt = synth.small_grid()
     net = _build(tt, trip=tt.trip, subtrips=scheme)
@@ -335,7 +336,7 @@ def test_build_csr_round_trip(make, width):
     a = _build(tt, cluster_width=width)
     b = eat.eat_build_csr(**csr_from_view(a), cluster_width=width, device=-1)
     va, vb = eat.eat_net_host_view(a), eat.eat_net_host_view(b)
-    for k in ("row_ptr", "type_rec", "cl", "ap", "cluster_entries", "ap_extra"):
+    for k in ("row_ptr", "type_rec", "cl", "ap", "cluster_entries", "ap_extra", "type_records"):
         assert np.array_equal(va[k], vb[k]), k
     sa, sb = eat.eat_get_stats(a), eat.eat_get_stats(b)
     for k in ("n_types", "n_edges", "n_ap", "y", "k_min", "max_out_types"):
@@ -343,7 +344,7 @@ def test_build_csr_round_trip(make, width):
 
 
 def test_build_csr_paper_example():
-    # Section III-C: departures 8:00, 8:15, ..., 18:00 as one AP when one cluster spans them.
+    # Section II-C: departures 8:00, 8:15, ..., 18:00 as one AP when one cluster spans them.
     net = eat.eat_build_csr(2, [0, 1, 1], [1], [60], [0, 1], [0], [0, 1], [28800], [900], [41],
                             cluster_width=65535, device=-1)
     st = eat.eat_get_stats(net)

@@ -1,5 +1,5 @@
-"""Topology-driven variants of Section III (eat_ladder_*): every variant gives the oracle's
-arrivals, with the flag read after every round or every few rounds (Section V-D)."""
+"""Topology-driven variants of Section II (eat_ladder_*): every variant gives the oracle's
+arrivals, with the flag read after every round or every few rounds (Section IV-C)."""
 import numpy as np
 import pytest
 

@@ -363,7 +363,7 @@ def test_ragged_64_networks_4096_queries(eat):
 
 @pytest.mark.parametrize("scheme", [1, 2])
 def test_subtrips_same_arrivals_fewer_rounds(eat, city, scheme):
-    """Section III-G: with sub-trip shortcuts the arrivals equal the oracle's on the original
+    """Section II-G: with sub-trip shortcuts the arrivals equal the oracle's on the original
     timetable, and queries need fewer rounds."""
     enh = Case(eat, city.tt, subtrips=scheme)
     q = synth.random_queries(city.tt, 256, 0x5B + scheme)
@@ -439,3 +439,38 @@ def test_lookup_through_count_overflow_header(eat):
     for t_s in (0, 5000, 59000):
         got = eat.eat_query(net, 0, t_s)
         assert np.array_equal(got, oracle.csa(oracle.SortedConnections(tt), 0, t_s))
+
+
+@pytest.mark.parametrize("vwarp", [1, 4, 8, 32])
+@pytest.mark.parametrize("block", [256, 1024])
+def test_edge_mode_matches_oracle(eat, small, city, vwarp, block):
+    """EAT_MODE_EDGE (a sub-warp of vwarp lanes per stop with at least vwarp types, one
+    relaxation per head stop after a warp min) gives the oracle's rows, on the packed
+    (small networks) and two-word items alike, with any sub-warp size."""
+    for case in (small, city):
+        q = synth.random_queries(case.tt, 96, 300 + vwarp)
+        got, status, cnt = case.run(eat, q.source, q.t_s, vwarp=vwarp, block=block,
+                                    mode=eat.EAT_MODE_EDGE)
+        assert (status == 0).all()
+        assert np.array_equal(got, case.oracle_rows(q.source, q.t_s))
+        for i in range(0, 96, 48):
+            assert oracle.certify(case.tt, int(q.source[i]), int(q.t_s[i]), got[i]) == (0, -1)
+    assert eat.eat_launch_shape(city.net, 96, mode=eat.EAT_MODE_EDGE)["mode"] == eat.EAT_MODE_EDGE
+
+
+def test_edge_mode_large_and_placements(eat, large_tt, large_sc):
+    """EAT_MODE_EDGE on the 200,000-stop network (arrivals in global memory) and with the
+    arrivals and bitmaps forced into global memory on the city network."""
+    import os
+    tt = large_tt
+    net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=0, cluster_width=1800)
+    q = synth.random_queries(tt, 256, 0x1E)
+    out = torch.empty(256 * tt.n_stops, dtype=torch.int32, device="cuda")
+    status = torch.full((256,), -1, dtype=torch.int32, device="cuda")
+    eat.eat_query_batch(net, _dev(q.source), _dev(q.t_s), out, status=status,
+                        mode=eat.EAT_MODE_EDGE, vwarp=8)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 0).all()
+    want, _ = oracle.csa_many(large_sc, q.source, q.t_s, os.cpu_count() or 8)
+    assert np.array_equal(out.view(256, tt.n_stops).cpu().numpy(), want)
+    net.close()

@@ -1,8 +1,9 @@
 """Serving loop (eat_server_*): continuous batching over resident networks.
 
 Each result must be identical whether the query runs alone (eat_query) or in
-the mix of a served stream, and the pool of in-flight batches must respect the
-device-memory budget.
+the mix of a served stream, in both admission modes (a ring of requests served by
+one running launch, or batches per slot), and what is in flight must respect the
+memory budget.
 """
 import threading
 import time
@@ -52,9 +53,10 @@ def _serve(eat, server, tts, qs, pace_s=0.0):
     return outs, got
 
 
-def test_served_results_equal_alone(eat, nets):
+@pytest.mark.parametrize("admission", [0, 1])
+def test_served_results_equal_alone(eat, nets, admission):
     tts, ns = nets
-    server = eat.Server(ns, max_batch=64, max_inflight=4)
+    server = eat.Server(ns, max_batch=64, max_inflight=4, admission=admission)
     qs = synth.random_queries(tts, 1500, 31)
     outs, got = _serve(eat, server, tts, qs)
     assert all(st == 0 for st, _ in got.values())
@@ -65,14 +67,47 @@ def test_served_results_equal_alone(eat, nets):
         want = oracle.csa(oracle.SortedConnections(tts[qs.net[i]]), int(qs.source[i]), int(qs.t_s[i]))
         assert np.array_equal(outs[i], want)
     st = server.stats()
-    assert st["completed"] == len(qs) and st["batches"] >= len(qs) // 64
-    assert st["max_batch_seen"] <= 64
+    assert st["completed"] == len(qs) and st["batched_queries"] == len(qs)
+    if admission == eat.EAT_ADMIT_BATCH:
+        assert st["batches"] >= len(qs) // 64 and st["max_batch_seen"] <= 64
+    else:
+        assert st["slots"] == 256 and st["max_inflight_seen"] <= 256 and st["batches"] >= 1
+    server.close()
+
+
+def test_ring_admits_into_a_running_launch(eat, nets):
+    """Ring admission: requests that arrive while the launch runs (paced submissions) enter
+    its ring and are served by it; each row equals the row of the same query run alone and
+    the oracle's.  A later burst after an idle gap starts a new launch."""
+    tts, ns = nets
+    server = eat.Server(ns, max_batch=16, max_inflight=4, admission=eat.EAT_ADMIT_RING)
+    qs = synth.random_queries(tts, 800, 35)
+    outs, got = _serve(eat, server, tts, qs, pace_s=0.0003)
+    assert all(st == 0 for st, _ in got.values())
+    st = server.stats()
+    assert st["slots"] == 64 and st["max_inflight_seen"] <= 64
+    assert st["admitted_running"] > 0
+    for i in range(len(qs)):
+        alone = eat.eat_query(ns[qs.net[i]], int(qs.source[i]), int(qs.t_s[i]))
+        assert np.array_equal(outs[i], alone), i
+    for i in range(0, len(qs), 41):
+        want = oracle.csa(oracle.SortedConnections(tts[qs.net[i]]), int(qs.source[i]), int(qs.t_s[i]))
+        assert np.array_equal(outs[i], want)
+    launches = st["batches"]
+    time.sleep(0.05)                                 # idle: the launch ends
+    qs2 = synth.random_queries(tts, 100, 36)
+    outs2, got2 = _serve(eat, server, tts, qs2)
+    assert server.stats()["batches"] > launches
+    for i in range(len(qs2)):
+        assert np.array_equal(outs2[i], eat.eat_query(ns[qs2.net[i]], int(qs2.source[i]),
+                                                        int(qs2.t_s[i])))
     server.close()
 
 
 def test_paced_arrivals_overlap_and_match(eat, nets):
     tts, ns = nets
-    server = eat.Server(ns, max_batch=32, max_inflight=3, batch_wait_us=100)
+    server = eat.Server(ns, max_batch=32, max_inflight=3, batch_wait_us=100,
+                        admission=eat.EAT_ADMIT_BATCH)
     qs = synth.random_queries(tts, 600, 32)
     outs, got = _serve(eat, server, tts, qs, pace_s=0.0005)
     for i in range(len(qs)):
@@ -84,15 +119,38 @@ def test_paced_arrivals_overlap_and_match(eat, nets):
     server.close()
 
 
+def test_ring_admission_by_memory(eat, nets):
+    """The ring holds as many requests as the budget allows beyond the launch's
+    workspace (rounded down to a power of two); no more are on the GPU at once."""
+    tts, ns = nets
+    with pytest.raises(eat.EatError) as ei:
+        eat.Server(ns, mem_budget=1000, admission=eat.EAT_ADMIT_RING)
+    assert ei.value.code == eat.EAT_ERR_OOM
+    probe = eat.Server(ns, admission=eat.EAT_ADMIT_RING)
+    pst = probe.stats()
+    probe.close()
+    budget = pst["base_bytes"] + 3 * pst["slot_bytes"] + pst["slot_bytes"] // 2
+    server = eat.Server(ns, mem_budget=budget, admission=eat.EAT_ADMIT_RING)
+    assert server.stats()["slots"] == 2
+    qs = synth.random_queries(tts, 200, 34)
+    outs, got = _serve(eat, server, tts, qs)
+    assert server.stats()["max_inflight_seen"] <= 2
+    for i in range(0, len(qs), 5):
+        assert np.array_equal(outs[i], eat.eat_query(ns[qs.net[i]], int(qs.source[i]),
+                                                       int(qs.t_s[i])))
+    server.close()
+
+
 def test_admission_by_memory(eat, nets):
     tts, ns = nets
     with pytest.raises(eat.EatError) as ei:
-        eat.Server(ns, max_batch=32, mem_budget=1000)
+        eat.Server(ns, max_batch=32, mem_budget=1000, admission=eat.EAT_ADMIT_BATCH)
     assert ei.value.code == eat.EAT_ERR_OOM
-    probe = eat.Server(ns, max_batch=32, max_inflight=1)
+    probe = eat.Server(ns, max_batch=32, max_inflight=1, admission=eat.EAT_ADMIT_BATCH)
     slot = probe.stats()["slot_bytes"]
     probe.close()
-    server = eat.Server(ns, max_batch=32, max_inflight=8, mem_budget=slot + slot // 2)
+    server = eat.Server(ns, max_batch=32, max_inflight=8, mem_budget=slot + slot // 2,
+                        admission=eat.EAT_ADMIT_BATCH)
     st = server.stats()
     assert st["slots"] == 1
     qs = synth.random_queries(tts, 300, 33)
@@ -104,9 +162,10 @@ def test_admission_by_memory(eat, nets):
     server.close()
 
 
-def test_invalid_submit_and_drain_on_close(eat, nets):
+@pytest.mark.parametrize("admission", [0, 1])
+def test_invalid_submit_and_drain_on_close(eat, nets, admission):
     tts, ns = nets
-    server = eat.Server(ns, max_batch=16)
+    server = eat.Server(ns, max_batch=16, admission=admission)
     buf = np.empty(tts[0].n_stops, np.int32)
     with pytest.raises(eat.EatError):
         server.submit(len(ns), 0, 0, buf, 1)

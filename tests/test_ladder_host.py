@@ -1,6 +1,6 @@
 """Host arrays of the topology-driven variants (built with device=-1, no GPU) against the
-oracle: the connection types and their sorted departures (Section III-B), the greedy AP
-cover of each type's whole day (Section II, Section III-C) and the edges (Section III-E)."""
+oracle: the connection types and their sorted departures (Section II-B), the greedy AP
+cover of each type's whole day (Section I-A, Section II-C) and the edges (Section II-E)."""
 import numpy as np
 import pytest
 

@@ -1,4 +1,4 @@
-"""Pins of oracle.connection_types, the type partition of Section III-B (no GPU).
+"""Pins of oracle.connection_types, the type partition of Section II-B (no GPU).
 
 A connection type C_{u,v,lambda} holds the connections of one edge (u, v) that share
 the duration lambda.  The oracle's partition is checked against

@@ -55,6 +55,33 @@ def test_noalloc_matches_batch_on_two_calls(eat, which):
     net.close()
 
 
+@pytest.mark.parametrize("which,opts", [
+    ("city", {"mode": 4}),          # paired mode: two queries per block, 16 bytes per stop
+    ("city", {"mode": 3}),          # round-free mode: no spill queues
+    ("small", {"placement": 3}),    # arrivals and bitmaps in global memory
+])
+def test_noalloc_other_layouts_match_batch_on_two_calls(eat, which, opts):
+    """The scratch is laid out differently by the paired mode, the round-free mode and
+    global bitmaps; each still returns what eat_query_batch returns, twice in a row."""
+    tt = synth.small_grid() if which == "small" else synth.city()
+    net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=0)
+    V = tt.n_stops
+    for call, seed in enumerate((21, 22)):
+        q = synth.random_queries(tt, 300, seed)
+        src, ts = _dev(q.source), _dev(q.t_s)
+        ref = torch.empty(300 * V, dtype=torch.int32, device="cuda")
+        eat.eat_query_batch(net, src, ts, ref, **opts)
+        got = torch.full((300 * V,), -1, dtype=torch.int32, device="cuda")
+        status = torch.full((300,), -1, dtype=torch.int32, device="cuda")
+        eat.eat_query_batch_noalloc(net, src, ts, got, status=status, **opts)
+        torch.cuda.synchronize()
+        assert (status.cpu().numpy() == 0).all(), call
+        assert torch.equal(got, ref), call
+    want, _ = oracle.csa_many(oracle.SortedConnections(tt), q.source, q.t_s, 8)
+    assert np.array_equal(got.view(300, V).cpu().numpy(), want)
+    net.close()
+
+
 def test_noalloc_rejects_what_it_cannot_serve(eat):
     tt = synth.small_grid()
     net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=0)
@@ -71,4 +98,9 @@ def test_noalloc_rejects_what_it_cannot_serve(eat):
     assert ei.value.code == eat.EAT_ERR_INVALID
     assert "no-allocation scratch" in str(ei.value)
     big.close()
+    if torch.cuda.device_count() > 1:               # a buffer on another GPU is refused
+        other = torch.empty(4 * tt.n_stops, dtype=torch.int32, device="cuda:1")
+        with pytest.raises(eat.EatError) as ei:
+            eat.eat_query_batch_noalloc(net, _dev(q.source), _dev(q.t_s), other)
+        assert ei.value.code == eat.EAT_ERR_INVALID
     net.close()
