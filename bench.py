@@ -57,12 +57,11 @@ FALLBACK_HBM_GBS = 6800.0
 BYTES = {"vertices": 20, "types": 28, "aps": 16, "relaxed": 12}
 
 # DRAM bytes per query of the timed kernel, from the ncu captures summarised in profiles/
-# (city: one 256-query launch, 1,024-thread blocks, started in order of t_s; large: one
-# 152-query launch, one query per SM, taken as
-# the per-query traffic of the 1,024-query step too); keyed by the kernel source hash
-# and the kernel's name, so that a changed kernel reports null until it is profiled again.
-NCU_TRAFFIC_PER_QUERY = {"city": ("aee99e7763a75c69", "eat_cta_kernel", 62338560 / 256),
-                         "large": ("aee99e7763a75c69", "eat_cta_kernel", 2690225104 / 152)}
+# (large: the bench's own 1,024-query launches, dram__bytes_read.sum +
+# dram__bytes_write.sum averaged over the 20 timed launches); keyed by the kernel source
+# hash and the kernel's name, so that a changed kernel reports null until it is profiled
+# again.
+NCU_TRAFFIC_PER_QUERY = {"large": ("0231113635555c16", "eat_cta_kernel", 25.872e9 / 1024)}
 KERNEL_OF_MODE = {1: "eat_cta_kernel", 2: "eat_cluster_kernel", 3: "eat_async_kernel",
                   4: "eat_pair_kernel", 5: "eat_cta_kernel"}
 

@@ -317,11 +317,15 @@ typedef struct {
  */
 int eat_build_csr(const eat_csr_input *in, const eat_build_opts *opts, eat_net **out);
 
-/* Release a network and its device memory.  NULL is ignored.  No query on the
- * network may be in flight. */
+/* Release a network and its device memory (no counterpart in the paper, which
+ * keeps one network for a process).  NULL is ignored.  No query on the network may
+ * be in flight. */
 void eat_free(eat_net *net);
 
-/* Sizes of a network.  Errors: EAT_ERR_INVALID on NULL arguments. */
+/* Sizes of a network: the counts of Section III-A's arrays (connection types,
+ * clusters, AP tuples; y is the paper's CL stride) and of Table I's statistics for
+ * the built network (stops, connections).  Named eat_get_stats because eat_stats is
+ * the struct's name.  Errors: EAT_ERR_INVALID on NULL arguments. */
 int eat_get_stats(const eat_net *net, eat_stats *out);
 
 /* Host view of the built arrays (see eat_net_view).  Works for host-only builds. */
