@@ -57,11 +57,13 @@ FALLBACK_HBM_GBS = 6800.0
 BYTES = {"vertices": 20, "types": 28, "aps": 16, "relaxed": 12}
 
 # DRAM bytes per query of the timed kernel, from the ncu captures summarised in profiles/
-# (large: the bench's own 1,024-query launches, dram__bytes_read.sum +
-# dram__bytes_write.sum averaged over the 20 timed launches); keyed by the kernel source
+# (the bench's own launches, dram__bytes_read.sum + dram__bytes_write.sum averaged over
+# the 20 timed launches: 1,024 queries on the large network, 256 on the city network);
+# keyed by the kernel source
 # hash and the kernel's name, so that a changed kernel reports null until it is profiled
 # again.
-NCU_TRAFFIC_PER_QUERY = {"large": ("0231113635555c16", "eat_cta_kernel", 25.872e9 / 1024)}
+NCU_TRAFFIC_PER_QUERY = {"large": ("0231113635555c16", "eat_cta_kernel", 25.872e9 / 1024),
+                         "city": ("0231113635555c16", "eat_cta_kernel", 58167693 / 256)}
 KERNEL_OF_MODE = {1: "eat_cta_kernel", 2: "eat_cluster_kernel", 3: "eat_async_kernel",
                   4: "eat_pair_kernel", 5: "eat_cta_kernel"}
 
