@@ -474,3 +474,24 @@ def test_edge_mode_large_and_placements(eat, large_tt, large_sc):
     want, _ = oracle.csa_many(large_sc, q.source, q.t_s, os.cpu_count() or 8)
     assert np.array_equal(out.view(256, tt.n_stops).cpu().numpy(), want)
     net.close()
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_tiny_nets_two_word_items(eat, seed):
+    """Two-word queue items (arrivals in global memory) on tiny random nets with narrow
+    clusters: the pushed types are filtered by their last departure against the cluster of
+    the new arrival, and a stop lowered into an earlier cluster after its push is pushed
+    again from its first item; every row equals the oracle's and brute force."""
+    tt = synth.tiny_random(3 + seed % 11, 20 + (seed * 53) % 400, 900 + seed, t_max=600 + 40 * seed,
+                           dur_max=1 + seed % 90)
+    case = Case(eat, tt, cluster_width=[30, 60, 120, 7][seed % 4])
+    src = np.repeat(np.arange(tt.n_stops), 3).astype(np.int32)
+    rng = np.random.default_rng(seed)
+    ts = rng.integers(-5, int(tt.dep.max()) + 10, size=src.shape[0]).astype(np.int32)
+    for placement in (eat.EAT_PLACE_GLOBAL_ARR, eat.EAT_PLACE_GLOBAL):
+        got, status, _ = case.run(eat, src, ts, placement=placement, block=64)
+        assert (status == 0).all()
+        assert np.array_equal(got, case.oracle_rows(src, ts))
+    for i in range(0, len(src), 5):
+        assert np.array_equal(got[i], oracle.brute.foremost_dijkstra(
+            tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, int(src[i]), int(ts[i])))
