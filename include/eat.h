@@ -157,7 +157,9 @@ typedef struct {
     int64_t lookups;   /* of the examined types, those whose cluster entry was read
                           (Section II-D); types >= lookups >= evals */
     int64_t aps;       /* AP records examined by the cluster lookup (Algorithm 6) */
-    int64_t relaxed;   /* successful lowerings of some e[v] (Algorithm 3) */
+    int64_t relaxed;   /* relaxations that lowered e[v] (Algorithm 3): candidates below
+                          the e[v] read just before the atomic min, so a candidate whose
+                          atomic lost to a lower one made meanwhile is counted too */
 } eat_counters;
 
 /* Query options.  Zero-initialise for defaults. */
