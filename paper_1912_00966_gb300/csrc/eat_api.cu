@@ -109,8 +109,9 @@ static int device_info(int dev, DeviceInfo &out) {
         DeviceGuard guard(dev);
         for (int nets : {1, EAT_MAX_NETS})
             for (int mem = 0; mem < 4; ++mem)
-                for (const void *k : {cta_kernel(nets, mem), async_kernel(nets, mem), cluster_kernel(),
-                                      cta_kernel(1, 0, true), pair_kernel(false), pair_kernel(true),
+                for (const void *k : {cta_kernel(nets, mem), cta_kernel(nets, mem, false, true),
+                                      async_kernel(nets, mem), cluster_kernel(), cta_kernel(1, 0, true),
+                                      cta_kernel(1, 0, true, true), pair_kernel(false), pair_kernel(true),
                                       ring_kernel(mem)}) {
                     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(d.smem_optin - d.reserve));

@@ -114,7 +114,9 @@ constexpr int32_t kNoSlot = 255;             // item tag: no cluster slot record
 // of at most 32,767 stops and 65,535 types), one word per item: first-item flag << 31 |
 // stop << 16 | type, which doubles the items a buffer holds in the same shared memory
 // (kNullItem is then no valid item: it would be stop 32,767, type 65,535).
-template <int NETS, int ARR, bool SMEM_MASK, bool PACK = false, bool RING = false>
+// COUNT: the build that fills qa.counters; without it the per-thread work counters are
+// dead code and compiled away (the timed launches pass no counters).
+template <int NETS, int ARR, bool SMEM_MASK, bool PACK = false, bool RING = false, bool COUNT = false>
 __global__ void __launch_bounds__(1024, 1)
 eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) {
     extern __shared__ __align__(16) int32_t smem[];
@@ -273,7 +275,10 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             // has a departure at or after e[u] (else it stops here, Section III-D).
             auto load_item = [&](int32_t i, int32_t &e_u, int32_t &k, int4 &ca, int4 &cb,
                                  int4 &tr) -> bool {
-                int32_t u, t, ks = kNoSlot;
+                // ks: the slot whose entry is loaded ahead, -1 for none (slot 255 is a
+                // valid slot on a network with more than 255 clusters, where items carry
+                // no slot).
+                int32_t u, t, ks = -1;
                 if (PACK) {
                     const int32_t raw = iu_rd[i];
                     if (raw == kNullItem) return false;
@@ -288,14 +293,17 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                     if (it.x == kNullItem) return false;
                     u = it.x & 0x7fffffff;
                     t = qa.spec ? it.y & 0xffffff : it.y;
-                    if (qa.spec) ks = (int32_t)((uint32_t)it.y >> 24);
+                    if (qa.spec) {
+                        ks = (int32_t)((uint32_t)it.y >> 24);
+                        if (ks == kNoSlot) ks = -1;
+                    }
                     if (it.x < 0) {
                         atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
                         ++c_vert;
                     }
                 }
                 ++c_types;
-                if (!PACK && ks != kNoSlot) load_entry(entry_at(N, ks, t), ca, cb);
+                if (!PACK && ks >= 0) load_entry(entry_at(N, ks, t), ca, cb);
                 tr = __ldg(N.tr + t);
                 e_u = load_arr(arr, u, arr_shared);
                 k = cluster_slot(N, e_u);
@@ -376,7 +384,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
         } else if (tid == 0 && qa.status) {
             qa.status[q] = q_status;
         }
-        if (!RING && qa.counters) {
+        if (COUNT && !RING && qa.counters) {
             unsigned long long c[6] = {(unsigned long long)c_vert, (unsigned long long)c_types,
                                        (unsigned long long)c_evals, (unsigned long long)c_lookups,
                                        (unsigned long long)c_aps, (unsigned long long)c_relax};
@@ -1162,19 +1170,22 @@ eat_cluster_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs 
     cluster.sync();                                   // block 0 is done reading the others
 }
 
-template <int NETS>
+template <int NETS, bool COUNT>
 static const void *cta_kernel_ptr(int mem) {
     switch (mem) {
-    case 0: return (const void *)eat_cta_kernel<NETS, kArrShared, true>;
-    case 1: return (const void *)eat_cta_kernel<NETS, kArrGlobal, true>;
-    case 3: return (const void *)eat_cta_kernel<NETS, kArrPerQuery, true>;
-    default: return (const void *)eat_cta_kernel<NETS, kArrGlobal, false>;
+    case 0: return (const void *)eat_cta_kernel<NETS, kArrShared, true, false, false, COUNT>;
+    case 1: return (const void *)eat_cta_kernel<NETS, kArrGlobal, true, false, false, COUNT>;
+    case 3: return (const void *)eat_cta_kernel<NETS, kArrPerQuery, true, false, false, COUNT>;
+    default: return (const void *)eat_cta_kernel<NETS, kArrGlobal, false, false, false, COUNT>;
     }
 }
 
-const void *cta_kernel(int nets, int mem, bool pack) {
-    if (pack) return (const void *)eat_cta_kernel<1, kArrShared, true, true>;
-    return nets == 1 ? cta_kernel_ptr<1>(mem) : cta_kernel_ptr<EAT_MAX_NETS>(mem);
+const void *cta_kernel(int nets, int mem, bool pack, bool count) {
+    if (pack)
+        return count ? (const void *)eat_cta_kernel<1, kArrShared, true, true, false, true>
+                     : (const void *)eat_cta_kernel<1, kArrShared, true, true, false, false>;
+    if (count) return nets == 1 ? cta_kernel_ptr<1, true>(mem) : cta_kernel_ptr<EAT_MAX_NETS, true>(mem);
+    return nets == 1 ? cta_kernel_ptr<1, false>(mem) : cta_kernel_ptr<EAT_MAX_NETS, false>(mem);
 }
 
 template <int NETS>
@@ -1210,31 +1221,36 @@ cudaError_t launch_async(const NetDev *nets, int n_nets, const QueryArgs &qa, in
     return launch_async_t<EAT_MAX_NETS>(nets, n_nets, qa, mem, grid, block, smem, st);
 }
 
-template <int NETS>
+template <int NETS, bool COUNT>
 static cudaError_t launch_cta_t(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem,
                                 int grid, int block, size_t smem, cudaStream_t st) {
     NetTable<NETS> tab;
     for (int i = 0; i < n_nets && i < NETS; ++i) tab.net[i] = nets[i];
     for (int i = n_nets; i < NETS; ++i) tab.net[i] = NetDev{};
     switch (mem) {
-    case 0: eat_cta_kernel<NETS, kArrShared, true><<<grid, block, smem, st>>>(tab, qa); break;
-    case 1: eat_cta_kernel<NETS, kArrGlobal, true><<<grid, block, smem, st>>>(tab, qa); break;
-    case 3: eat_cta_kernel<NETS, kArrPerQuery, true><<<grid, block, smem, st>>>(tab, qa); break;
-    default: eat_cta_kernel<NETS, kArrGlobal, false><<<grid, block, smem, st>>>(tab, qa); break;
+    case 0: eat_cta_kernel<NETS, kArrShared, true, false, false, COUNT><<<grid, block, smem, st>>>(tab, qa); break;
+    case 1: eat_cta_kernel<NETS, kArrGlobal, true, false, false, COUNT><<<grid, block, smem, st>>>(tab, qa); break;
+    case 3: eat_cta_kernel<NETS, kArrPerQuery, true, false, false, COUNT><<<grid, block, smem, st>>>(tab, qa); break;
+    default: eat_cta_kernel<NETS, kArrGlobal, false, false, false, COUNT><<<grid, block, smem, st>>>(tab, qa); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
                        int block, size_t smem, cudaStream_t st, bool pack) {
+    const bool count = qa.counters != nullptr;
     if (pack) {
         NetTable<1> tab;
         tab.net[0] = nets[0];
-        eat_cta_kernel<1, kArrShared, true, true><<<grid, block, smem, st>>>(tab, qa);
+        if (count) eat_cta_kernel<1, kArrShared, true, true, false, true><<<grid, block, smem, st>>>(tab, qa);
+        else eat_cta_kernel<1, kArrShared, true, true, false, false><<<grid, block, smem, st>>>(tab, qa);
         return cudaGetLastError();
     }
-    if (n_nets == 1) return launch_cta_t<1>(nets, n_nets, qa, mem, grid, block, smem, st);
-    return launch_cta_t<EAT_MAX_NETS>(nets, n_nets, qa, mem, grid, block, smem, st);
+    if (n_nets == 1)
+        return count ? launch_cta_t<1, true>(nets, n_nets, qa, mem, grid, block, smem, st)
+                     : launch_cta_t<1, false>(nets, n_nets, qa, mem, grid, block, smem, st);
+    return count ? launch_cta_t<EAT_MAX_NETS, true>(nets, n_nets, qa, mem, grid, block, smem, st)
+                 : launch_cta_t<EAT_MAX_NETS, false>(nets, n_nets, qa, mem, grid, block, smem, st);
 }
 
 const void *ring_kernel(int mem) {

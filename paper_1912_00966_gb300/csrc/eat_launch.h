@@ -71,7 +71,9 @@ struct QueryArgs {
 // the query's network fits.  nets: 1 or EAT_MAX_NETS (kernel table size).
 // pack: one int32 per item (one network of at most 32,767 stops and 65,535 types,
 // arrivals and bitmaps in shared memory).
-const void *cta_kernel(int nets, int mem, bool pack = false);
+// count: the instantiation that fills qa.counters (launch_cta picks it when counters are
+// given).
+const void *cta_kernel(int nets, int mem, bool pack = false, bool count = false);
 cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
                        int block, size_t smem, cudaStream_t st, bool pack = false);
 // Ring mode of the per-query kernel (serving): persistent blocks take requests from

@@ -303,6 +303,35 @@ def test_cluster_widths(eat, width):
     assert np.array_equal(got, case.oracle_rows(q.source, q.t_s))
 
 
+@pytest.mark.parametrize("width", [60, 200])
+@pytest.mark.parametrize("placement", [2, 3])    # arrivals in global memory: two-word items
+def test_more_than_255_cluster_slots(eat, width, placement):
+    """With more than 255 cluster slots an item carries no cluster slot of its own, and
+    the entry of slot 255 (a valid slot here) is loaded from the stop's arrival like any
+    other: rows equal the oracle's for queries whose arrivals pass through that slot."""
+    tt = synth.small_grid(seed_offset=7)
+    case = Case(eat, tt, cluster_width=width)
+    st = eat.eat_get_stats(case.net)
+    assert st["y"] > 255
+    q = synth.random_queries(tt, 192, 0x255 + width)
+    slot255 = (st["k_min"] + 255) * width         # start of slot 255 (t0 = 0)
+    assert (q.t_s < slot255).sum() >= 24          # many queries start before it
+    got, status, _ = case.run(eat, q.source, q.t_s, placement=placement)
+    assert (status == 0).all()
+    assert np.array_equal(got, case.oracle_rows(q.source, q.t_s))
+
+
+def test_city_at_300_second_clusters(eat):
+    """The city network with 300-second clusters (about 285 slots), default launch."""
+    tt = synth.city()
+    case = Case(eat, tt, cluster_width=300)
+    assert eat.eat_get_stats(case.net)["y"] > 255
+    q = synth.random_queries(tt, 96, 0x300)
+    got, status, _ = case.run(eat, q.source, q.t_s)
+    assert (status == 0).all()
+    assert np.array_equal(got, case.oracle_rows(q.source, q.t_s))
+
+
 def test_large_network_all_rows(eat, large_tt, large_sc):
     """200,000-stop network, about 46 M connections, 1,024 queries in one launch: every row
     equals the oracle's, with the library's default launch and 60-minute clusters, and with
