@@ -106,9 +106,9 @@ def run_ours_ragged(args):
     out = torch.empty(total, dtype=torch.int32, device="cuda")
     cnt = torch.zeros((n_steps, Q, 7), dtype=torch.int64, device="cuda")
     status = torch.zeros((n_steps, Q), dtype=torch.int32, device="cuda")
-    opts = dict(vwarp=args.vwarp, block=args.block, mode=args.mode)
+    opts = dict(vwarp=args.vwarp, block=args.block, mode=args.mode, horizon=args.horizon)
     tuned = None
-    if args.autotune and not (args.vwarp or args.block or args.mode):
+    if args.autotune and not (args.vwarp or args.block or args.mode or args.horizon):
         # Launch shape and start order chosen by the library's multi-network autotuner on
         # a sample batch (setup, untimed).
         sample = synth.random_queries(tts, Q, 0xA0 - 1)
@@ -251,7 +251,7 @@ def run_ours_ragged(args):
         "cpu_baseline": cpu,
         "sequential_plain_queries": {"value": plain_n / plain_s, "unit": "queries/s",
                                      "queries": plain_n},
-        "launch_shape": {**{k: shape[k] for k in ("block", "vwarp", "mode", "order")},
+        "launch_shape": {**{k: shape[k] for k in ("block", "vwarp", "mode", "order", "horizon")},
                          "chosen_by": "autotuner" if tuned else "library default or flags"},
         "cluster_width_s": args.cluster_width,
         "work_per_query": {n: tot[n] / (Q * args.steps) for n in names},
@@ -670,9 +670,9 @@ def run_ours(args):
     out = torch.empty(batch * V, dtype=torch.int32, device="cuda")
     cnt = torch.zeros((n_steps, batch, 7), dtype=torch.int64, device="cuda")
     status = torch.zeros((n_steps, batch), dtype=torch.int32, device="cuda")
-    opts = dict(vwarp=args.vwarp, block=args.block, mode=args.mode)
+    opts = dict(vwarp=args.vwarp, block=args.block, mode=args.mode, horizon=args.horizon)
     tuned = None
-    if args.autotune and not (args.vwarp or args.block or args.mode):
+    if args.autotune and not (args.vwarp or args.block or args.mode or args.horizon):
         # Launch shape chosen by the library's autotuner on a sample batch (setup, untimed).
         sample = synth.random_queries(tt, batch, 0xB0 - 1)
         tuned = eat.eat_autotune(net, torch.as_tensor(sample.source).cuda(),
@@ -837,7 +837,7 @@ def run_ours(args):
         "csa_equivalent_connections_per_s": csa_conn / (gpu_s / world),
         "subtrips": {0: "none", 1: "sqrt(k) per trip", 2: "sqrt(mean trip length)"}[args.subtrips],
         "cluster_width_s": args.cluster_width,
-        "launch_shape": {**{k: shape[k] for k in ("block", "vwarp", "mode")},
+        "launch_shape": {**{k: shape[k] for k in ("block", "vwarp", "mode", "order", "horizon")},
                          "chosen_by": "autotuner" if tuned else "library default or flags"},
         "without_subtrips": None if base_ms is None else
             {"value": batch / (base_ms / 1e3), "unit": "queries/s", "ms_per_step": base_ms},
@@ -878,9 +878,12 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--mode", type=int, default=0,
                     help="0 auto, 1 rounds, 3 asynchronous, 4 paired, 5 edge min + degree mapping")
+    ap.add_argument("--horizon", type=int, default=0,
+                    help="seconds; 0 the tuned value (else none), -1 none (every improved stop "
+                         "expanded next round, Algorithms 4-5)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
-    ap.add_argument("--cluster-width", type=int, default=1800,
+    ap.add_argument("--cluster-width", type=int, default=600,
                     help="seconds per departure cluster (Section II-D uses one hour; Section IV-B finds narrower clusters faster)")
     ap.add_argument("--subtrips", type=int, default=0, choices=[0, 1, 2],
                     help="sub-trip shortcuts (Section II-G): 0 none, 1 sqrt(k), 2 sqrt(mean)")

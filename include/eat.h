@@ -165,7 +165,9 @@ typedef struct {
 /* Query options.  Zero-initialise for defaults. */
 typedef struct {
     int32_t max_rounds;      /* round cap; 0 = n_stops + 1 (always enough: every
-                                productive round fixes at least one more stop) */
+                                productive round fixes at least one more stop), or
+                                2 * n_stops + 2 with a horizon (each horizon step adds at
+                                most one round to the n_stops + 1) */
     int32_t block;           /* threads per CTA: 0 = automatic (the tuned shape, else 1024
                                 when the batch has at most one query per SM, runs in the
                                 paired mode or is on one network of 8,192 stops or more,
@@ -184,6 +186,21 @@ typedef struct {
                                 hold work gives up the query, which then reports
                                 EAT_ERR_NO_CONVERGENCE with upper bounds in its row;
                                 0 = 2^24 (far beyond any wait of a correct run) */
+    int32_t horizon;         /* seconds; the per-query kernel's rounds (EAT_MODE_CTA or
+                                EAT_MODE_EDGE) expand a stop lowered to an arrival at or
+                                after the horizon H only once no stop below H is left to
+                                expand; H starts at t_s + horizon and then moves to the
+                                earliest arrival still waiting + horizon.  The arrivals
+                                are the same (the fixpoint does not depend on the order
+                                of relaxations); stops first reached late by a path of
+                                few connections are then expanded once, with an arrival
+                                closer to their final one, instead of again each time a
+                                later round improves them (Algorithms 4-5 expand every
+                                improved stop in the next round).
+                                0 = automatic (the value eat_autotune chose for this
+                                batch size, else none); < 0 = none; > 0 with
+                                EAT_MODE_PAIR, EAT_MODE_ASYNC or EAT_MODE_CLUSTER is
+                                EAT_ERR_INVALID */
     int32_t *status;         /* optional [n] per-query eat_status, device memory */
     eat_counters *counters;  /* optional [n] per-query counters, device memory */
 } eat_query_opts;
@@ -360,8 +377,9 @@ size_t eat_workspace_bytes(const eat_net *const *nets, int32_t n_nets, int32_t n
  * eat_launch_shape -- the launch shape eat_query_batch(_multi) would use for n
  * queries over the given networks with these options (opts may be NULL): *shape
  * receives a copy of *opts with block, vwarp, mode (EAT_MODE_CTA, _CLUSTER,
- * _ASYNC or _PAIR, never _AUTO), cluster and order (EAT_ORDER_BY_TIME or
- * EAT_ORDER_AS_GIVEN, never _AUTO) filled in.  Nothing is launched.
+ * _ASYNC, _PAIR or _EDGE, never _AUTO), cluster, order (EAT_ORDER_BY_TIME or
+ * EAT_ORDER_AS_GIVEN, never _AUTO) and horizon (seconds, -1 for none, never 0)
+ * filled in.  Nothing is launched.
  * Returns EAT_OK, or the error the batch call would report for these options.
  */
 int eat_launch_shape(const eat_net *const *nets, int32_t n_nets, int32_t n,
@@ -437,7 +455,9 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
  * mode, then with EAT_MODE_EDGE and vwarp 8 and 32, as far as they fit the device
  * (1024 threads first on networks of 8,192 stops or more and for batches of at most
  * one query per SM, where it is the default); when n exceeds the SM count, then the
- * paired mode with vwarp 8, 4 and 16.  They are run on the sample batch
+ * paired mode with vwarp 8, 4 and 16; then the round-based mode with the first two
+ * block sizes, vwarp 8 and horizons of 1, 2, 4 and 12 hours (the other candidates run
+ * with none).  They are run on the sample batch
  * sources/times (n queries, device memory) in nine rounds over all candidates:
  * the first warms up, the other eight are timed with CUDA events on `stream`,
  * each after a write of twice the L2 size so that every timing starts with the
@@ -446,10 +466,11 @@ int eat_next_departure(const eat_net *net, const int32_t *types, const int32_t *
  * batches of one workload), and
  * is stored for batches of about n queries in the network; afterwards every
  * query call that leaves opts->block, opts->vwarp and opts->mode at 0 uses it
- * (a call with a round cap keeps the round-based mode).  The tuned shape is
- * written to *best (may be NULL).  Blocks until done.  Allocates its own
- * scratch (workspace, output rows and the cache-flush buffer) for the duration
- * of the call.  Errors: as eat_query_batch; EAT_ERR_INVALID if no shape fits.
+ * (a call with a round cap keeps the round-based mode), and every call that leaves
+ * opts->horizon at 0 and runs the round-based kernel uses its horizon.  The tuned
+ * shape (block, vwarp, mode, horizon: -1 for none) is written to *best (may be
+ * NULL).  Blocks until done.  Allocates its own scratch (workspace, output rows and
+ * the cache-flush buffer) for the duration of the call.  Errors: as eat_query_batch; EAT_ERR_INVALID if no shape fits.
  */
 int eat_autotune(eat_net *net, const int32_t *sources, const int32_t *times, int32_t n,
                  eat_query_opts *best, void *stream);
@@ -460,12 +481,14 @@ int eat_autotune(eat_net *net, const int32_t *sources, const int32_t *times, int
  * paper, as for eat_autotune.  Candidates, in this order: start order as given, then by
  * t_s (EAT_ORDER_AS_GIVEN, EAT_ORDER_BY_TIME); for each, block sizes 512, 1024 and 256
  * threads, each with the round-based mode and vwarp 8, 4, 16, 2, 32, then the
- * asynchronous mode, then EAT_MODE_EDGE with vwarp 8; shapes without a plan for these
- * networks are skipped.  They run on
+ * asynchronous mode, then EAT_MODE_EDGE with vwarp 8; then the round-based mode with 512
+ * threads, vwarp 8, start by t_s and horizons of 2 and 12 hours (the others run with
+ * none); shapes without a plan for these networks are skipped.  They run on
  * the sample batch (net_idx, sources, times: [n] int32 device memory; rows packed in
  * query order in a scratch buffer) and are timed as eat_autotune times them (nine rounds,
  * cold L2, median, earliest within 5 % wins).  Nothing is stored in the networks: the
- * caller passes *best (block, vwarp, mode and order filled in, the rest zero) as the
+ * caller passes *best (block, vwarp, mode, order and horizon filled in, the rest zero,
+ * horizon -1 for none) as the
  * options of its eat_query_batch_multi calls.  Blocks until done; allocates its scratch
  * for the duration of the call.
  * Errors: EAT_ERR_INVALID (NULL best, bad networks or indices, host arrays, no shape

@@ -111,7 +111,8 @@ static int device_info(int dev, DeviceInfo &out) {
             for (int mem = 0; mem < 4; ++mem)
                 for (const void *k : {cta_kernel(nets, mem), cta_kernel(nets, mem, false, true),
                                       async_kernel(nets, mem), cluster_kernel(), cta_kernel(1, 0, true),
-                                      cta_kernel(1, 0, true, true), pair_kernel(false), pair_kernel(true),
+                                      cta_kernel(1, 0, true, true), cta_kernel(1, 0, true, false, true),
+                                      cta_kernel(1, 0, true, true, true), pair_kernel(false), pair_kernel(true),
                                       ring_kernel(mem)}) {
                     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(d.smem_optin - d.reserve));
@@ -148,11 +149,20 @@ struct Plan {
     bool edge = false;            // warp min per head stop, degree-chosen mapping (EAT_MODE_EDGE)
     bool order = false;           // queries start by t_s (EAT_ORDER_BY_TIME): order array at off_order
     size_t off_order = 0;
+    int32_t horizon = 0;          // seconds (eat_query_opts.horizon resolved), 0 = none
 };
 
 static constexpr size_t kWsHeader = 256;   // work counter + internal status / counters
 static constexpr int32_t kDefaultIdleCap = 1 << 24;   // round-free mode's wait limit (full scans)
 static constexpr size_t kQueueEntryBytes = 16;  // (stop, type) item x 2 buffers
+
+// Default round cap: n_stops + 1 rounds always reach the fixpoint (every productive round
+// fixes one more stop); with a horizon, each move of the horizon can add one round in
+// which only stops released from waiting are expanded, at most n_stops of them.
+static int32_t default_round_cap(int32_t vmax, int32_t horizon) {
+    const int64_t cap = horizon > 0 ? 2 * (int64_t)vmax + 2 : (int64_t)vmax + 1;
+    return (int32_t)std::min<int64_t>(cap, INT32_MAX);
+}
 
 // Plan of the round-free kernel: arrivals (shared when they fit), one bitmap and
 // a 512-byte staging area per warp in shared memory; no spill queues.
@@ -316,14 +326,15 @@ static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const ea
     if (rc) return rc;
     p.nets = n_nets == 1 ? 1 : EAT_MAX_NETS;
     p.vmax = vmax;
-    int tb = 0, tv = 0, tm = 0;
+    int tb = 0, tv = 0, tm = 0, th = 0;
     if (tuned && n > 0) {
         int cls = 0;
         while (cls < 31 && (1 << (cls + 1)) <= n) ++cls;
-        const uint32_t sh = tuned->tuned[cls].load(std::memory_order_relaxed);
+        const uint64_t sh = tuned->tuned[cls].load(std::memory_order_relaxed);
         tb = (int)(sh & 0xffffu);
         tv = (int)((sh >> 16) & 0xffu);
-        tm = (int)(sh >> 24);
+        tm = (int)((sh >> 24) & 0xffu);
+        th = (int)(uint32_t)(sh >> 32);
     }
     // Default shape: a 1,024-thread block per query when the batch has at most one query
     // per SM, or on one network of 8,192 stops or more (there the batch starts in order
@@ -347,6 +358,9 @@ static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const ea
         return fail(EAT_ERR_INVALID, "mode must be one of EAT_MODE_*");
     p.edge = (o && o->mode == EAT_MODE_EDGE) ||
              (tm == EAT_MODE_EDGE && !(o && o->mode != EAT_MODE_AUTO));
+    const int32_t oh = o ? o->horizon : 0;
+    if (oh > 0 && (o->mode == EAT_MODE_PAIR || o->mode == EAT_MODE_ASYNC || o->mode == EAT_MODE_CLUSTER))
+        return fail(EAT_ERR_INVALID, "a horizon needs the per-query kernel's rounds (EAT_MODE_CTA or EAT_MODE_EDGE)");
     if (o && o->mode == EAT_MODE_PAIR) {
         if (n_nets != 1) return fail(EAT_ERR_INVALID, "paired mode serves one network per launch");
         if (o->placement != EAT_PLACE_AUTO && o->placement != EAT_PLACE_SHARED)
@@ -361,7 +375,8 @@ static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const ea
         if (!own_workspace) return fail(EAT_ERR_INVALID, "cluster mode is not available here");
         return make_cluster_plan(dev, d, vmax, n, o, p);
     }
-    const bool rounds_needed = o && o->max_rounds > 0;   // the round cap needs rounds
+    // The round cap and the horizon need the per-query kernel's rounds.
+    const bool rounds_needed = o && (o->max_rounds > 0 || o->horizon > 0);
     if ((o && o->mode == EAT_MODE_ASYNC) ||
         (tm == EAT_MODE_ASYNC && !rounds_needed && (!o || o->mode == EAT_MODE_AUTO)))
         return make_async_plan(dev, d, vmax, n, n_nets, o, p, vmin);
@@ -374,7 +389,7 @@ static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const ea
     const bool explicit_block = o && o->block;
     if ((!o || o->mode == EAT_MODE_AUTO) && own_workspace && n_nets == 1 && tuned &&
         (place == EAT_PLACE_AUTO || place == EAT_PLACE_SHARED) && !explicit_block &&
-        tm == EAT_MODE_PAIR) {
+        tm == EAT_MODE_PAIR && oh <= 0) {
         Plan q = p;
         q.block = tb ? tb : 1024;
         if (make_pair_plan(dev, d, vmax, n, tuned, q) == EAT_OK) {
@@ -418,6 +433,7 @@ static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const ea
     // Items take one int32 instead of two on one network small enough for the packed
     // form (twice the queue in the same shared memory).
     p.pack = p.mem == 0 && n_nets == 1 && tuned && vmax <= 32767 && tuned->host.n_types <= 65535;
+    p.horizon = oh > 0 ? oh : (oh == 0 ? th : 0);
     const size_t qbytes = p.pack ? kQueueEntryBytes / 2 : kQueueEntryBytes;
     // Largest queue capacity that keeps the most blocks per SM the threads and the
     // registers allow (shared memory is the only other limit, and the one sized here).
@@ -425,8 +441,8 @@ static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const ea
     int reg_blocks = 0;
     {
         DeviceGuard guard(dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&reg_blocks, cta_kernel(p.nets, p.mem, p.pack),
-                                                          p.block, 0) != cudaSuccess) {
+        const void *k = cta_kernel(p.nets, p.mem, p.pack, false, p.horizon > 0);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&reg_blocks, k, p.block, 0) != cudaSuccess) {
             cudaGetLastError();
             reg_blocks = 0;
         }
@@ -450,13 +466,15 @@ static int make_plan_core(int dev, int32_t vmax, int32_t n, int n_nets, const ea
     cudaError_t e;
     {
         DeviceGuard guard(dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cta_kernel(p.nets, p.mem, p.pack),
-                                                          p.block, p.smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, cta_kernel(p.nets, p.mem, p.pack, false, p.horizon > 0), p.block, p.smem);
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) return fail(EAT_ERR_INVALID, "kernel does not fit on an SM with this block size");
     p.grid = (int)std::min<int64_t>((int64_t)std::max(n, 1), (int64_t)per_sm * d.sms);
-    p.spill_stride = (int64_t)align_up((size_t)vmax * 2, 64);
+    // With a horizon a block also keeps two lists of waiting stops and their bitmap.
+    p.spill_stride = p.horizon > 0 ? (int64_t)align_up((size_t)vmax * 4 + (size_t)p.mask_words, 64)
+                                   : (int64_t)align_up((size_t)vmax * 2, 64);
     p.mask_stride = p.mem == 2 ? (int64_t)align_up(2 * (size_t)p.mask_words, 64) : 0;
     p.off_spill = kWsHeader;
     p.off_mask = p.off_spill + (size_t)p.grid * (size_t)p.spill_stride * 4;
@@ -520,10 +538,10 @@ static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net
     qa.arr_rows = nullptr;
     qa.arr_rows_stride = 0;
     qa.order = p.order ? (const int32_t *)(ws + p.off_order) : nullptr;
-    qa.spec = 0;
     qa.idle_cap = kDefaultIdleCap;
     qa.rg = RingArgs{};
     qa.edge = p.edge ? 1 : 0;
+    qa.horizon = p.horizon;
     return qa;
 }
 
@@ -531,15 +549,6 @@ static QueryArgs make_args(const Plan &p, int grid, char *ws, const int32_t *net
 // and the output rows are host memory (0 when every query's arrivals are shared).
 static size_t arr_rows_bytes(const Plan &p) {
     return p.mem == 0 ? 0 : (size_t)p.grid * align_up((size_t)p.vmax, 64) * 4;
-}
-
-// Whether the per-query kernel's two-word items can carry the cluster slot of their
-// stop's arrival at push time (type | slot << 24): every network of the launch has
-// fewer than 2^24 connection types and at most 255 cluster slots (slot 255 = none).
-static bool spec_items(const eat_net *const *nets, int n_nets) {
-    for (int i = 0; i < n_nets; ++i)
-        if (nets[i]->host.n_types >= (1 << 24) || nets[i]->host.y > 255) return false;
-    return true;
 }
 
 static int ensure_buffer(void *&buf, size_t &cap, size_t need) {
@@ -576,11 +585,10 @@ static int run_batch(const eat_net *const *nets, int n_nets, const int32_t *net_
         return fail(EAT_ERR_WORKSPACE, "workspace of " + std::to_string(ws_bytes) +
                                            " bytes, need " + std::to_string(p.ws_bytes));
     if (n == 0) return EAT_OK;
-    const int32_t cap = (o && o->max_rounds > 0) ? o->max_rounds : (vmax < INT32_MAX ? vmax + 1 : vmax);
+    const int32_t cap = (o && o->max_rounds > 0) ? o->max_rounds : default_round_cap(vmax, p.horizon);
     QueryArgs qa = make_args(p, p.grid, (char *)ws, net_idx, src, ts, n, n_nets, arr_out, arr_off,
                              cap, status_override ? status_override : (o ? o->status : nullptr),
                              counters_override ? counters_override : (o ? o->counters : nullptr));
-    qa.spec = spec_items(nets, n_nets) ? 1 : 0;
     if (o && o->idle_cap > 0) qa.idle_cap = o->idle_cap;
     if (arr_rows && p.mem != 0) {
         if (arr_rows_size < arr_rows_bytes(p)) return fail(EAT_ERR_INVALID, "arrival rows too small");
@@ -665,8 +673,7 @@ int ring_launch(const eat_net *const *nets, int n_nets, const RingLaunch &rl, vo
     p.spill_stride = rl.spill_stride;
     p.mask_stride = 0;
     QueryArgs qa = make_args(p, rl.grid, (char *)ws, nullptr, nullptr, nullptr, 0, n_nets, pool,
-                             nullptr, rl.vmax < INT32_MAX ? rl.vmax + 1 : rl.vmax, nullptr, nullptr);
-    qa.spec = spec_items(nets, n_nets) ? 1 : 0;
+                             nullptr, default_round_cap(rl.vmax, p.horizon), nullptr, nullptr);
     qa.rg = rg;
     if (rl.mem != 0) {
         qa.arr_rows = arr_rows;
@@ -900,6 +907,7 @@ int eat_launch_shape(const eat_net *const *nets, int32_t n_nets, int32_t n,
                   : p.async ? EAT_MODE_ASYNC : p.edge ? EAT_MODE_EDGE : EAT_MODE_CTA;
     shape->cluster = p.cluster;
     shape->order = p.order ? EAT_ORDER_BY_TIME : EAT_ORDER_AS_GIVEN;
+    shape->horizon = p.horizon > 0 ? p.horizon : -1;
     return EAT_OK;
 }
 
@@ -1163,6 +1171,7 @@ namespace eat {
 
 struct TuneCand {
     int m, b, v, ord;            // mode, block, vwarp, start order (EAT_ORDER_*)
+    int h;                       // horizon (s), 0 = none
     std::vector<float> ms;
 };
 
@@ -1172,6 +1181,7 @@ static eat_query_opts cand_opts(const TuneCand &cd) {
     o.vwarp = cd.v;
     o.mode = cd.m;
     o.order = cd.ord;
+    o.horizon = cd.h > 0 ? cd.h : -1;    // none, not a horizon tuned earlier
     return o;
 }
 
@@ -1294,20 +1304,24 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
         eat_query_opts o{};
         o.mode = EAT_MODE_PAIR;
         if (eat_workspace_bytes(nets, 1, n, &o))
-            for (int v : {8, 4, 16}) pairs.push_back({EAT_MODE_PAIR, 1024, v, EAT_ORDER_AUTO, {}});
+            for (int v : {8, 4, 16}) pairs.push_back({EAT_MODE_PAIR, 1024, v, EAT_ORDER_AUTO, 0, {}});
         else clear_error();                  // network too large for two rows per block
     }
     const bool wide = net->host.n_stops >= kWideMinStops || n <= dinfo.sms;
     for (int b : {wide ? 1024 : 512, wide ? 512 : 1024, 256}) {
-        for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, EAT_ORDER_AUTO, {}});
-        cands.push_back({EAT_MODE_ASYNC, b, 8, EAT_ORDER_AUTO, {}});
-        for (int v : {8, 32}) cands.push_back({EAT_MODE_EDGE, b, v, EAT_ORDER_AUTO, {}});
+        for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, EAT_ORDER_AUTO, 0, {}});
+        cands.push_back({EAT_MODE_ASYNC, b, 8, EAT_ORDER_AUTO, 0, {}});
+        for (int v : {8, 32}) cands.push_back({EAT_MODE_EDGE, b, v, EAT_ORDER_AUTO, 0, {}});
     }
     cands.insert(cands.end(), pairs.begin(), pairs.end());
+    // Horizons (1, 2, 4 and 12 hours) with the first two block sizes and vwarp 8.
+    for (int b : {wide ? 1024 : 512, wide ? 512 : 1024})
+        for (int h : {3600, 7200, 14400, 43200})
+            cands.push_back({EAT_MODE_CTA, b, 8, EAT_ORDER_AUTO, h, {}});
     size_t ws_need = 0;
     int rc = usable_candidates(nets, 1, n, cands, ws_need);
     if (rc) return rc;
-    TuneCand win{EAT_MODE_CTA, 512, 8, EAT_ORDER_AUTO, {}};
+    TuneCand win{EAT_MODE_CTA, 512, 8, EAT_ORDER_AUTO, 0, {}};
     rc = time_candidates(net->device, cands, ws_need, (size_t)n * (size_t)net->host.n_stops * 4, st,
                          [&](const eat_query_opts &o, void *ws, size_t wsb, int32_t *rows) {
                              return run_batch(nets, 1, nullptr, sources, times, n, rows, nullptr,
@@ -1317,13 +1331,15 @@ extern "C" int eat_autotune(eat_net *net, const int32_t *sources, const int32_t 
     if (rc) return rc;
     int cls = 0;
     while (cls < 31 && (1 << (cls + 1)) <= n) ++cls;
-    net->tuned[cls].store((uint32_t)win.b | (uint32_t)win.v << 16 | (uint32_t)win.m << 24,
+    net->tuned[cls].store((uint64_t)win.b | (uint64_t)win.v << 16 | (uint64_t)win.m << 24 |
+                              (uint64_t)(uint32_t)win.h << 32,
                           std::memory_order_relaxed);
     if (best) {
         *best = eat_query_opts{};
         best->block = win.b;
         best->vwarp = win.v;
         best->mode = win.m;
+        best->horizon = win.h > 0 ? win.h : -1;
     }
     return EAT_OK;
 }
@@ -1372,18 +1388,20 @@ extern "C" int eat_autotune_multi(const eat_net *const *nets, int32_t n_nets, co
     }
     // Candidates in a fixed order, the library's default for a batch over several
     // networks first (512 threads, vwarp 8, index order): block sizes 512, 1,024 and
-    // 256, each with vwarp 8, 4, 16, 2, 32 and the round-free mode, each in index
-    // order and then in order of t_s.
+    // 256, each with vwarp 8, 4, 16, 2, 32, the round-free mode and the edge mode, each
+    // in index order and then in order of t_s; then horizons of 2 and 12 hours (512
+    // threads, vwarp 8, in order of t_s).
     std::vector<TuneCand> cands;
     for (int ord : {EAT_ORDER_AS_GIVEN, EAT_ORDER_BY_TIME})
         for (int b : {512, 1024, 256}) {
-            for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, ord, {}});
-            cands.push_back({EAT_MODE_ASYNC, b, 8, ord, {}});
-            cands.push_back({EAT_MODE_EDGE, b, 8, ord, {}});
+            for (int v : {8, 4, 16, 2, 32}) cands.push_back({EAT_MODE_CTA, b, v, ord, 0, {}});
+            cands.push_back({EAT_MODE_ASYNC, b, 8, ord, 0, {}});
+            cands.push_back({EAT_MODE_EDGE, b, 8, ord, 0, {}});
         }
+    for (int h : {7200, 43200}) cands.push_back({EAT_MODE_CTA, 512, 8, EAT_ORDER_BY_TIME, h, {}});
     size_t ws_need = 0;
     int rc = usable_candidates(nets, n_nets, n, cands, ws_need);
-    TuneCand win{EAT_MODE_CTA, 512, 8, EAT_ORDER_AS_GIVEN, {}};
+    TuneCand win{EAT_MODE_CTA, 512, 8, EAT_ORDER_AS_GIVEN, 0, {}};
     if (!rc)
         rc = time_candidates(dev, cands, ws_need, (size_t)total * 4, st,
                              [&](const eat_query_opts &o, void *ws, size_t wsb, int32_t *rows) {
@@ -1398,6 +1416,7 @@ extern "C" int eat_autotune_multi(const eat_net *const *nets, int32_t n_nets, co
     best->vwarp = win.v;
     best->mode = win.m;
     best->order = win.ord;
+    best->horizon = win.h > 0 ? win.h : -1;
     return EAT_OK;
 }
 
@@ -1460,11 +1479,11 @@ extern "C" int eat_query_batch_noalloc(const eat_net *net, const int32_t *source
     void *scratch = nullptr;
     rc = noalloc_scratch(net->device, &scratch);
     if (rc) return rc;
-    const int32_t cap = (opts && opts->max_rounds > 0) ? opts->max_rounds : net->host.n_stops + 1;
+    const int32_t cap = (opts && opts->max_rounds > 0) ? opts->max_rounds
+                                                       : default_round_cap(net->host.n_stops, p.horizon);
     QueryArgs qa = make_args(p, grid, (char *)scratch, nullptr, sources, times, n, 1, arr_out,
                              nullptr, cap, opts ? opts->status : nullptr,
                              opts ? opts->counters : nullptr);
-    qa.spec = spec_items(&net, 1) ? 1 : 0;
     if (opts && opts->idle_cap > 0) qa.idle_cap = opts->idle_cap;
     cudaStream_t st = (cudaStream_t)stream;
     // The query counter must start at zero; the queues need no clearing.

@@ -91,9 +91,9 @@ struct eat_net {
     mutable void *stage = nullptr;
     mutable size_t stage_bytes = 0;
     // Launch shape chosen by eat_autotune per batch-size class (log2 of n), packed as
-    // block | vwarp << 16 | mode << 24 (0 = none) so that a query call on another
-    // thread reads one whole shape.
-    mutable std::atomic<uint32_t> tuned[32] = {};
+    // block | vwarp << 16 | mode << 24 | horizon << 32 (0 = none) so that a query call
+    // on another thread reads one whole shape.
+    mutable std::atomic<uint64_t> tuned[32] = {};
 };
 
 namespace eat {

@@ -23,14 +23,23 @@
 // writes one (v, type) item per connection type leaving v into shared memory (one
 // 32- or 64-bit store each), so the next round hands every thread one (stop, type)
 // pair: the paper's one thread per connection type (Algorithm 5), restricted to the
-// active tails.  Per item, the type's 16-byte
-// record (head, duration, head row, last departure), e[u] and the 32-byte cluster
-// entry of e[u]'s cluster (whose address depends only on the type and the cluster;
-// two-word items carry the cluster at push time so that this load need not wait for
-// e[u]) are loaded together, then e[v] beside any further APs: two dependent global
-// round trips when arrivals live in global memory, one when they are in shared
-// memory.  Stops whose items do not fit spill to a global queue and are expanded by
-// `vwarp`-lane sub-warps (Section II-F's virtual warps).
+// active tails.  Per item, the type's 16-byte record (head, duration, head row, last
+// departure) and e[u] are loaded together, then the 32-byte cluster entry of e[u]'s
+// cluster, then e[v] beside any further APs.  Stops whose items do not fit spill to a
+// global queue and are expanded by `vwarp`-lane sub-warps (Section II-F's virtual
+// warps).
+//
+// Horizon (qa.horizon > 0, an option; not in the paper): Algorithms 4-5 expand every
+// improved stop in the next round, so a stop first reached late by a path of few
+// connections is expanded, and its successors with it, again each time a later round
+// improves it.  With a horizon H a stop lowered to an arrival >= H is not queued but
+// waits (once, in a per-block list with a bitmap); when no stop below H is left to
+// expand, waiting stops whose arrival has since dropped below H are dropped (they
+// were queued by that lowering), H moves to the earliest remaining arrival + horizon,
+// and the stops below the new H become the next round's spilled stops.  Every
+// lowered stop is still expanded with its arrival at some round after the lowering,
+// so the fixpoint is the same; only the order of relaxations changes (as
+// delta-stepping orders Bellman-Ford's).
 //
 // Buffers per query: arrivals in shared memory (ARR = kArrShared), in global
 // memory (kArrGlobal: the output row, or the block's scratch row when the output
@@ -108,15 +117,16 @@ __device__ __forceinline__ void ring_done(const RingArgs &R, int32_t slot, int32
 
 constexpr int32_t kNullItem = -1;           // hole left by a stop that spilled
 constexpr int32_t kFirstItem = INT32_MIN;    // flag on the first item of a stop
-constexpr int32_t kNoSlot = 255;             // item tag: no cluster slot recorded
 
 // Items are (stop, type) pairs in two int32 arrays per buffer, or, with PACK (networks
 // of at most 32,767 stops and 65,535 types), one word per item: first-item flag << 31 |
 // stop << 16 | type, which doubles the items a buffer holds in the same shared memory
 // (kNullItem is then no valid item: it would be stop 32,767, type 65,535).
 // COUNT: the build that fills qa.counters; without it the per-thread work counters are
-// dead code and compiled away (the timed launches pass no counters).
-template <int NETS, int ARR, bool SMEM_MASK, bool PACK = false, bool RING = false, bool COUNT = false>
+// dead code and compiled away (the timed launches pass no counters).  HZ: the build that
+// honours qa.horizon (the packed build also comes without, for launches with none).
+template <int NETS, int ARR, bool SMEM_MASK, bool PACK = false, bool RING = false, bool COUNT = false,
+          bool HZ = true>
 __global__ void __launch_bounds__(1024, 1)
 eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) {
     extern __shared__ __align__(16) int32_t smem[];
@@ -125,6 +135,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
     __shared__ int32_t s_items[3];    // items reserved per round (rotating)
     __shared__ int32_t s_spill[3];    // stops spilled per round (rotating)
     __shared__ unsigned long long s_cnt[6];
+    __shared__ int32_t s_def[4];      // waiting stops: count, kept, released, least arrival
 
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -139,6 +150,9 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
     int32_t *const spill_base = qa.spill + (int64_t)blockIdx.x * qa.spill_stride;
     uint32_t *const mask_base = SMEM_MASK ? (uint32_t *)(smem + qa.smem_mask_off)
                                           : qa.gmask + (int64_t)blockIdx.x * qa.mask_stride;
+    // Stops waiting beyond the horizon: two lists of vmax stops and their bitmap.
+    int32_t *const def_base = spill_base + 2 * (int64_t)qa.vmax;
+    uint32_t *const dmask = (uint32_t *)(spill_base + 4 * (int64_t)qa.vmax);
 
     for (;;) {
         if (tid == 0) s_q = RING ? ring_next(qa.rg, s_ring) : next_query(qa);
@@ -171,10 +185,14 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             mask0[i] = 0u;
             mask1[i] = 0u;
         }
+        const bool hz_on = HZ && qa.horizon > 0;
+        if (hz_on)
+            for (int32_t i = tid; i < nwords; i += nthr) dmask[i] = 0u;
         if (tid < 3) {
             s_items[tid] = 0;
             s_spill[tid] = 0;
         }
+        if (tid == 0) s_def[0] = 0;
         const int32_t s = RING ? s_ring[1] : __ldg(qa.src + q);
         const int32_t t_s = RING ? s_ring[2] : __ldg(qa.ts + q);
         const bool valid = net_ok && (unsigned)s < (unsigned)V;
@@ -189,11 +207,15 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
 
         int32_t n_items = 0, n_spill = valid ? 1 : 0;
         int32_t rounds = 0;
+        // Horizon H (kInf when there is none): a stop lowered to an arrival at or after
+        // H waits until no stop below H is left to expand.
+        int32_t H = hz_on && t_s < kInf - qa.horizon ? t_s + qa.horizon : kInf;
+        int dl = 0;                                       // list that new waiting stops join
         int cs = 0;                                       // counter slot written this round
         int32_t c_vert = 0, c_types = 0, c_evals = 0, c_lookups = 0, c_aps = 0, c_relax = 0;
         while (n_items + n_spill > 0 && rounds < qa.max_rounds) {
             const int wr = rounds & 1, rd = wr ^ 1;
-            // One-word items (PACK) or two-word items {stop | first flag, type | tag}.
+            // One-word items (PACK) or two-word items {stop | first flag, type}.
             int32_t *const iu_rd = item_base + (PACK ? rd : 2 * rd) * icap;
             int32_t *const iu_wr = item_base + (PACK ? wr : 2 * wr) * icap;
             const int2 *const i2_rd = reinterpret_cast<const int2 *>(iu_rd);
@@ -238,6 +260,11 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                 if (d == kCountOverflow) d = __ldg(N.row_ptr + v + 1) - tr.z;
                 if (d <= 0) return;
                 const uint32_t bit = 1u << (v & 31);
+                if (HZ && cand >= H) {                      // beyond the horizon: wait
+                    if (!(atomicOr(dmask + (v >> 5), bit) & bit))
+                        def_base[(int64_t)dl * qa.vmax + atomicAdd(&s_def[0], 1)] = v;
+                    return;
+                }
                 if (atomicOr(pmask + (v >> 5), bit) & bit) return;   // already queued
                 if (qa.edge && d >= vw) {                   // a sub-warp expands v whole
                     sp_wr[atomicAdd(&s_spill[cs], 1)] = v;
@@ -257,57 +284,40 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
                     iu_wr[base] = hv | kFirstItem;
                     for (int32_t j = 1; j < d; ++j) iu_wr[base + j] = hv + j;
                 } else {
-                    // The cluster slot of v's arrival now, for next round's entry load.
-                    int32_t tag = 0;
-                    if (qa.spec) {
-                        const int32_t kv = cluster_slot(N, cand);
-                        tag = (int32_t)((uint32_t)(kv < N.y ? kv : kNoSlot) << 24);
-                    }
-                    i2_wr[base] = make_int2(v | kFirstItem, tr.z | tag);
-                    for (int32_t j = 1; j < d; ++j) i2_wr[base + j] = make_int2(v, (tr.z + j) | tag);
+                    i2_wr[base] = make_int2(v | kFirstItem, tr.z);
+                    for (int32_t j = 1; j < d; ++j) i2_wr[base + j] = make_int2(v, tr.z + j);
                 }
             };
             // Item i: its stop u and type t (clearing u's bit in last round's bitmap at
-            // u's first item); loads the type record, e[u] and the cluster entry together:
-            // two-word items tagged with a cluster slot load that slot's entry at once and
-            // load again only when e[u] has since moved to another cluster; others load the
-            // entry of e[u]'s cluster as soon as e[u] is known.  Returns whether the type
-            // has a departure at or after e[u] (else it stops here, Section III-D).
+            // u's first item); loads the type record and e[u], then the cluster entry of
+            // e[u]'s cluster.  Returns whether the type has a departure at or after e[u]
+            // (else it stops here, Section III-D).
             auto load_item = [&](int32_t i, int32_t &e_u, int32_t &k, int4 &ca, int4 &cb,
                                  int4 &tr) -> bool {
-                // ks: the slot whose entry is loaded ahead, -1 for none (slot 255 is a
-                // valid slot on a network with more than 255 clusters, where items carry
-                // no slot).
-                int32_t u, t, ks = -1;
+                int32_t u, t;
+                bool first;
                 if (PACK) {
                     const int32_t raw = iu_rd[i];
                     if (raw == kNullItem) return false;
                     u = (raw >> 16) & 0x7fff;
                     t = raw & 0xffff;
-                    if (raw < 0) {
-                        atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
-                        ++c_vert;
-                    }
+                    first = raw < 0;
                 } else {
                     const int2 it = i2_rd[i];
                     if (it.x == kNullItem) return false;
                     u = it.x & 0x7fffffff;
-                    t = qa.spec ? it.y & 0xffffff : it.y;
-                    if (qa.spec) {
-                        ks = (int32_t)((uint32_t)it.y >> 24);
-                        if (ks == kNoSlot) ks = -1;
-                    }
-                    if (it.x < 0) {
-                        atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
-                        ++c_vert;
-                    }
+                    t = it.y;
+                    first = it.x < 0;
+                }
+                if (first) {
+                    atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
+                    ++c_vert;
                 }
                 ++c_types;
-                if (!PACK && ks >= 0) load_entry(entry_at(N, ks, t), ca, cb);
                 tr = __ldg(N.tr + t);
                 e_u = load_arr(arr, u, arr_shared);
                 k = cluster_slot(N, e_u);
-                if ((PACK || k != ks) && k < N.y) load_entry(entry_at(N, k, t), ca, cb);
+                if (k < N.y) load_entry(entry_at(N, k, t), ca, cb);
                 return e_u <= tr.w;
             };
 
@@ -370,6 +380,45 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             n_spill = s_spill[cs];
             cs = cs == 2 ? 0 : cs + 1;
             ++rounds;
+            if (hz_on && n_items + n_spill == 0 && s_def[0] > 0) {
+                // No stop below H is left: waiting stops since lowered below H were
+                // queued by that lowering and drop out; H moves to the earliest remaining
+                // arrival + horizon and the stops below it become next round's spilled
+                // stops, the others wait on (in the other list).
+                const int32_t nd = s_def[0];
+                const int32_t *const L = def_base + (int64_t)dl * qa.vmax;
+                int32_t *const K = def_base + (int64_t)(dl ^ 1) * qa.vmax;
+                int32_t *const sp_next = spill_base + (int64_t)((rounds & 1) ^ 1) * qa.vmax;
+                if (tid == 0) {
+                    s_def[1] = 0;
+                    s_def[2] = 0;
+                    s_def[3] = kInf;
+                }
+                __syncthreads();
+                int32_t m = kInf;
+                for (int32_t i = tid; i < nd; i += nthr) {
+                    const int32_t e = load_arr(arr, __ldcg(L + i), arr_shared);
+                    if (e >= H) m = min(m, e);
+                }
+                m = __reduce_min_sync(0xffffffffu, m);
+                if ((tid & 31) == 0 && m < kInf) atomicMin(&s_def[3], m);
+                __syncthreads();
+                const int32_t lo = s_def[3];
+                const int32_t Hn = lo < kInf - qa.horizon ? lo + qa.horizon : kInf;
+                for (int32_t i = tid; i < nd; i += nthr) {
+                    const int32_t v = __ldcg(L + i);
+                    const int32_t e = load_arr(arr, v, arr_shared);
+                    if (e < H) continue;
+                    if (e < Hn) sp_next[atomicAdd(&s_def[2], 1)] = v;
+                    else K[atomicAdd(&s_def[1], 1)] = v;
+                }
+                __syncthreads();
+                n_spill = s_def[2];
+                H = Hn;
+                dl ^= 1;
+                if (tid == 0) s_def[0] = s_def[1];   // no thread reads [0] or [1] before this
+                __syncthreads();
+            }
         }
         const int32_t F = n_items + n_spill;
 
@@ -1180,10 +1229,14 @@ static const void *cta_kernel_ptr(int mem) {
     }
 }
 
-const void *cta_kernel(int nets, int mem, bool pack, bool count) {
-    if (pack)
-        return count ? (const void *)eat_cta_kernel<1, kArrShared, true, true, false, true>
-                     : (const void *)eat_cta_kernel<1, kArrShared, true, true, false, false>;
+const void *cta_kernel(int nets, int mem, bool pack, bool count, bool hz) {
+    if (pack) {
+        if (hz)
+            return count ? (const void *)eat_cta_kernel<1, kArrShared, true, true, false, true, true>
+                         : (const void *)eat_cta_kernel<1, kArrShared, true, true, false, false, true>;
+        return count ? (const void *)eat_cta_kernel<1, kArrShared, true, true, false, true, false>
+                     : (const void *)eat_cta_kernel<1, kArrShared, true, true, false, false, false>;
+    }
     if (count) return nets == 1 ? cta_kernel_ptr<1, true>(mem) : cta_kernel_ptr<EAT_MAX_NETS, true>(mem);
     return nets == 1 ? cta_kernel_ptr<1, false>(mem) : cta_kernel_ptr<EAT_MAX_NETS, false>(mem);
 }
@@ -1242,8 +1295,11 @@ cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int 
     if (pack) {
         NetTable<1> tab;
         tab.net[0] = nets[0];
-        if (count) eat_cta_kernel<1, kArrShared, true, true, false, true><<<grid, block, smem, st>>>(tab, qa);
-        else eat_cta_kernel<1, kArrShared, true, true, false, false><<<grid, block, smem, st>>>(tab, qa);
+        const bool hz = qa.horizon > 0;
+        if (count && hz) eat_cta_kernel<1, kArrShared, true, true, false, true, true><<<grid, block, smem, st>>>(tab, qa);
+        else if (count) eat_cta_kernel<1, kArrShared, true, true, false, true, false><<<grid, block, smem, st>>>(tab, qa);
+        else if (hz) eat_cta_kernel<1, kArrShared, true, true, false, false, true><<<grid, block, smem, st>>>(tab, qa);
+        else eat_cta_kernel<1, kArrShared, true, true, false, false, false><<<grid, block, smem, st>>>(tab, qa);
         return cudaGetLastError();
     }
     if (n_nets == 1)

@@ -58,12 +58,12 @@ struct QueryArgs {
     int64_t arr_rows_stride;   // ints per block row
     const int32_t *order;      // [n]: the i-th query handed out is order[i], or nullptr (i)
     int32_t idle_cap;          // round-free mode: empty 32-word bitmap scans in a row per warp
-    int32_t spec;              // two-word items carry the cluster slot of the head's arrival
-                               // at push time (type | slot << 24): every network of the
-                               // launch has < 2^24 types and <= 255 cluster slots
     RingArgs rg;               // ring mode only
     int32_t edge;              // EAT_MODE_EDGE: warp min per head stop, stops with >= vwarp
                                // types expanded whole by a sub-warp
+    int32_t horizon;           // seconds, 0 = none: stops lowered to an arrival at or after
+                               // the horizon wait (per-query kernel); with one,
+                               // spill_stride >= 4 * vmax + mask_words
 };
 
 // mem: 0 = arrivals and bitmaps in shared memory, 1 = arrivals global / bitmaps
@@ -72,8 +72,9 @@ struct QueryArgs {
 // pack: one int32 per item (one network of at most 32,767 stops and 65,535 types,
 // arrivals and bitmaps in shared memory).
 // count: the instantiation that fills qa.counters (launch_cta picks it when counters are
-// given).
-const void *cta_kernel(int nets, int mem, bool pack = false, bool count = false);
+// given); hz: with pack, the instantiation that honours qa.horizon (launch_cta picks it
+// when qa.horizon > 0; the others always honour it).
+const void *cta_kernel(int nets, int mem, bool pack = false, bool count = false, bool hz = false);
 cudaError_t launch_cta(const NetDev *nets, int n_nets, const QueryArgs &qa, int mem, int grid,
                        int block, size_t smem, cudaStream_t st, bool pack = false);
 // Ring mode of the per-query kernel (serving): persistent blocks take requests from

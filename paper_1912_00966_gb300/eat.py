@@ -85,8 +85,8 @@ class eat_query_opts(ctypes.Structure):
     _fields_ = [("max_rounds", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("vwarp", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("placement", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("order", ctypes.c_int32), ("idle_cap", ctypes.c_int32), ("status", _vp),
-                ("counters", _vp)]
+                ("order", ctypes.c_int32), ("idle_cap", ctypes.c_int32),
+                ("horizon", ctypes.c_int32), ("status", _vp), ("counters", _vp)]
 
 
 class eat_server_opts(ctypes.Structure):
@@ -316,9 +316,10 @@ def eat_net_host_view(net: Net) -> dict:
 
 
 def _opts(max_rounds=0, block=0, vwarp=0, mode=0, placement=0, cluster=0, order=0, idle_cap=0,
-          status=None, counters=None):
+          horizon=0, status=None, counters=None):
     return eat_query_opts(int(max_rounds), int(block), int(vwarp), int(mode), int(placement),
-                          int(cluster), int(order), int(idle_cap), _ptr(status), _ptr(counters))
+                          int(cluster), int(order), int(idle_cap), int(horizon), _ptr(status),
+                          _ptr(counters))
 
 
 def eat_query(net: Net, s: int, t_s: int, out=None, counters: bool = False):
@@ -342,7 +343,8 @@ def eat_workspace_bytes(nets, n, **opts) -> int:
 
 
 def eat_launch_shape(nets, n, **opts) -> dict:
-    """Launch shape a batch of n queries would run with: block, vwarp, mode, cluster, order."""
+    """Launch shape a batch of n queries would run with: block, vwarp, mode, cluster, order,
+    horizon (-1 = none)."""
     if isinstance(nets, Net):
         nets = [nets]
     arr = (_vp * len(nets))(*[x.handle.value for x in nets])
@@ -351,7 +353,7 @@ def eat_launch_shape(nets, n, **opts) -> dict:
     _check(_lib.eat_launch_shape(arr, len(nets), int(n), ctypes.byref(o), ctypes.byref(shape)),
            "eat_launch_shape")
     return {"block": shape.block, "vwarp": shape.vwarp, "mode": shape.mode, "cluster": shape.cluster,
-            "order": shape.order}
+            "order": shape.order, "horizon": shape.horizon}
 
 
 def eat_query_batch(net: Net, sources, times, out, workspace=None, workspace_bytes=None,
@@ -396,23 +398,25 @@ def eat_query_batch_noalloc(net: Net, sources, times, out, stream=None, **opts):
 
 def eat_autotune(net: Net, sources, times, stream=None) -> dict:
     """Time the candidate launch shapes on a sample batch (device int32 arrays) and keep the
-    fastest for this network and batch size; returns {"block": b, "vwarp": v, "mode": m}."""
+    fastest for this network and batch size; returns {"block", "vwarp", "mode", "horizon"}
+    (horizon -1 = none)."""
     o = eat_query_opts()
     _check(_lib.eat_autotune(net.handle, _ptr(sources), _ptr(times), int(sources.shape[0]),
                              ctypes.byref(o), _stream_handle(stream)), "eat_autotune")
-    return {"block": o.block, "vwarp": o.vwarp, "mode": o.mode}
+    return {"block": o.block, "vwarp": o.vwarp, "mode": o.mode, "horizon": o.horizon}
 
 
 def eat_autotune_multi(nets, net_idx, sources, times, stream=None) -> dict:
     """Time the candidate launch shapes and start orders of a batch over several networks
-    (device int32 arrays); returns {"block", "vwarp", "mode", "order"} to pass as the
-    options of eat_query_batch_multi."""
+    (device int32 arrays); returns {"block", "vwarp", "mode", "order", "horizon"} to pass
+    as the options of eat_query_batch_multi."""
     arr = (_vp * len(nets))(*[x.handle.value for x in nets])
     o = eat_query_opts()
     _check(_lib.eat_autotune_multi(arr, len(nets), _ptr(net_idx), _ptr(sources), _ptr(times),
                                    int(sources.shape[0]), ctypes.byref(o), _stream_handle(stream)),
            "eat_autotune_multi")
-    return {"block": o.block, "vwarp": o.vwarp, "mode": o.mode, "order": o.order}
+    return {"block": o.block, "vwarp": o.vwarp, "mode": o.mode, "order": o.order,
+            "horizon": o.horizon}
 
 
 def eat_next_departure(net: Net, types, times, out, stream=None):

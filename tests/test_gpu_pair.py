@@ -160,13 +160,13 @@ def test_launch_shape_defaults(eat, small, city):
     batches on small networks; the paired mode only when asked for (or tuned)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert eat.eat_launch_shape(city.net, sms + 1) == {"block": 1024, "vwarp": 8, "mode": 1, "cluster": 0,
-                                                       "order": eat.EAT_ORDER_BY_TIME}
+                                                       "order": eat.EAT_ORDER_BY_TIME, "horizon": -1}
     assert eat.eat_launch_shape(small.net, sms + 1)["block"] == 512
     assert eat.eat_launch_shape(small.net, sms + 1, mode=PAIR)["mode"] == PAIR
     assert eat.eat_launch_shape(city.net, sms + 1, mode=PAIR)["block"] == 1024
     for case in (small, city):
         assert eat.eat_launch_shape(case.net, sms) == {"block": 1024, "vwarp": 8, "mode": 1, "cluster": 0,
-                                                       "order": eat.EAT_ORDER_AS_GIVEN}
+                                                       "order": eat.EAT_ORDER_AS_GIVEN, "horizon": -1}
         assert eat.eat_launch_shape(case.net, 4 * sms, block=512)["mode"] == 1
         assert eat.eat_launch_shape(case.net, 4 * sms, mode=3)["mode"] == 3
     other = eat.eat_build(small.tt.n_stops, small.tt.u, small.tt.v, small.tt.dep, small.tt.dur,

@@ -306,9 +306,9 @@ def test_cluster_widths(eat, width):
 @pytest.mark.parametrize("width", [60, 200])
 @pytest.mark.parametrize("placement", [2, 3])    # arrivals in global memory: two-word items
 def test_more_than_255_cluster_slots(eat, width, placement):
-    """With more than 255 cluster slots an item carries no cluster slot of its own, and
-    the entry of slot 255 (a valid slot here) is loaded from the stop's arrival like any
-    other: rows equal the oracle's for queries whose arrivals pass through that slot."""
+    """More than 255 cluster slots, two-word queue items: rows equal the oracle's for
+    queries whose arrivals pass through slot 255 and beyond (an earlier version used
+    slot 255 as a 'none' marker in its items and skipped that slot's entry load)."""
     tt = synth.small_grid(seed_offset=7)
     case = Case(eat, tt, cluster_width=width)
     st = eat.eat_get_stats(case.net)
@@ -334,25 +334,26 @@ def test_city_at_300_second_clusters(eat):
 
 def test_large_network_all_rows(eat, large_tt, large_sc):
     """200,000-stop network, about 46 M connections, 1,024 queries in one launch: every row
-    equals the oracle's, with the library's default launch and 60-minute clusters, and with
-    30-minute clusters in the launch shape the autotuner picks (the benchmark's setup)."""
+    equals the oracle's, with the library's default launch and 60-minute clusters, with
+    10-minute clusters in the launch shape the autotuner picks (the benchmark's setup),
+    and with 10-minute clusters and a 2-hour horizon."""
     import os
     tt = large_tt
     q = synth.random_queries(tt, 1024, 0x1A)
     want, _ = oracle.csa_many(large_sc, q.source, q.t_s, os.cpu_count() or 8)
-    for width, tune in ((3600, False), (1800, True)):
+    for width, tune, opts in ((3600, False, {}), (600, True, {}), (600, False, {"horizon": 7200})):
         net = eat.eat_build(tt.n_stops, tt.u, tt.v, tt.dep, tt.dur, device=0, cluster_width=width)
         if tune:
             sample = synth.random_queries(tt, 1024, 0x1A - 1)
             eat.eat_autotune(net, _dev(sample.source), _dev(sample.t_s))
         out = torch.empty(1024 * tt.n_stops, dtype=torch.int32, device="cuda")
         status = torch.full((1024,), -1, dtype=torch.int32, device="cuda")
-        eat.eat_query_batch(net, _dev(q.source), _dev(q.t_s), out, status=status)
+        eat.eat_query_batch(net, _dev(q.source), _dev(q.t_s), out, status=status, **opts)
         torch.cuda.synchronize()
         assert (status.cpu().numpy() == 0).all()
         got = out.view(1024, tt.n_stops).cpu().numpy()
         bad = np.nonzero((got != want).any(axis=1))[0]
-        assert bad.size == 0, (width, bad[:8])
+        assert bad.size == 0, (width, tune, opts, bad[:8])
         del out
         net.close()
     for i in (0, 511, 1023):
@@ -365,7 +366,7 @@ def test_ragged_64_networks_4096_queries(eat):
     batch, default launch shape); every row equals the oracle's."""
     import os
     tts = synth.ragged_grids(64)
-    nets = [eat.eat_build(t.n_stops, t.u, t.v, t.dep, t.dur, device=0, cluster_width=1800)
+    nets = [eat.eat_build(t.n_stops, t.u, t.v, t.dep, t.dur, device=0, cluster_width=600)
             for t in tts]
     Q = 4096
     qs = synth.random_queries(tts, Q, 0xA0 + 5)
