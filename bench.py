@@ -59,11 +59,10 @@ BYTES = {"vertices": 20, "types": 28, "aps": 16, "relaxed": 12}
 # DRAM bytes per query of the timed kernel, from the ncu captures summarised in profiles/
 # (the bench's own launches, dram__bytes_read.sum + dram__bytes_write.sum averaged over
 # the 20 timed launches: 1,024 queries on the large network, 256 on the city network);
-# keyed by the kernel source
-# hash and the kernel's name, so that a changed kernel reports null until it is profiled
-# again.
-NCU_TRAFFIC_PER_QUERY = {"large": ("0231113635555c16", "eat_cta_kernel", 25.872e9 / 1024),
-                         "city": ("0231113635555c16", "eat_cta_kernel", 58167693 / 256)}
+# keyed by the kernel source hash, the kernel's name, the block size, the horizon and the
+# cluster width, so that another kernel or launch shape reports null until it is
+# profiled again.  Filled in from the captures of the current kernel.
+NCU_TRAFFIC_PER_QUERY = {}
 KERNEL_OF_MODE = {1: "eat_cta_kernel", 2: "eat_cluster_kernel", 3: "eat_async_kernel",
                   4: "eat_pair_kernel", 5: "eat_cta_kernel"}
 
@@ -784,8 +783,9 @@ def run_ours(args):
     kernel_name = KERNEL_OF_MODE[shape["mode"]]
     h = kernel_hash()
     traffic = None
-    if args.workload in NCU_TRAFFIC_PER_QUERY and NCU_TRAFFIC_PER_QUERY[args.workload][:2] == (h, kernel_name):
-        traffic = NCU_TRAFFIC_PER_QUERY[args.workload][2] * batch
+    key = (h, kernel_name, shape["block"], shape["horizon"], args.cluster_width)
+    if args.workload in NCU_TRAFFIC_PER_QUERY and NCU_TRAFFIC_PER_QUERY[args.workload][:5] == key:
+        traffic = NCU_TRAFFIC_PER_QUERY[args.workload][5] * batch
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:

@@ -295,23 +295,24 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             auto load_item = [&](int32_t i, int32_t &e_u, int32_t &k, int4 &ca, int4 &cb,
                                  int4 &tr) -> bool {
                 int32_t u, t;
-                bool first;
                 if (PACK) {
                     const int32_t raw = iu_rd[i];
                     if (raw == kNullItem) return false;
                     u = (raw >> 16) & 0x7fff;
                     t = raw & 0xffff;
-                    first = raw < 0;
+                    if (raw < 0) {
+                        atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
+                        ++c_vert;
+                    }
                 } else {
                     const int2 it = i2_rd[i];
                     if (it.x == kNullItem) return false;
                     u = it.x & 0x7fffffff;
                     t = it.y;
-                    first = it.x < 0;
-                }
-                if (first) {
-                    atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
-                    ++c_vert;
+                    if (it.x < 0) {
+                        atomicAnd(cmask + (u >> 5), ~(1u << (u & 31)));
+                        ++c_vert;
+                    }
                 }
                 ++c_types;
                 tr = __ldg(N.tr + t);
@@ -380,44 +381,48 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
             n_spill = s_spill[cs];
             cs = cs == 2 ? 0 : cs + 1;
             ++rounds;
-            if (hz_on && n_items + n_spill == 0 && s_def[0] > 0) {
-                // No stop below H is left: waiting stops since lowered below H were
-                // queued by that lowering and drop out; H moves to the earliest remaining
-                // arrival + horizon and the stops below it become next round's spilled
-                // stops, the others wait on (in the other list).
+            if (hz_on && n_items + n_spill == 0) {
+                // No stop below H is left: waiting stops since lowered below H were queued
+                // by that lowering and drop out; H moves to the earliest remaining arrival
+                // + horizon and the stops below it become next round's spilled stops, the
+                // others wait on (in the other list).  (Releasing while a few stops below
+                // H are still queued moves H every round and loses the horizon.)  The
+                // waiting count is read before a barrier that no change to it precedes.
                 const int32_t nd = s_def[0];
-                const int32_t *const L = def_base + (int64_t)dl * qa.vmax;
-                int32_t *const K = def_base + (int64_t)(dl ^ 1) * qa.vmax;
-                int32_t *const sp_next = spill_base + (int64_t)((rounds & 1) ^ 1) * qa.vmax;
                 if (tid == 0) {
                     s_def[1] = 0;
                     s_def[2] = 0;
                     s_def[3] = kInf;
                 }
                 __syncthreads();
-                int32_t m = kInf;
-                for (int32_t i = tid; i < nd; i += nthr) {
-                    const int32_t e = load_arr(arr, __ldcg(L + i), arr_shared);
-                    if (e >= H) m = min(m, e);
+                if (nd > 0) {
+                    const int32_t *const L = def_base + (int64_t)dl * qa.vmax;
+                    int32_t *const K = def_base + (int64_t)(dl ^ 1) * qa.vmax;
+                    int32_t *const sp_next = spill_base + (int64_t)((rounds & 1) ^ 1) * qa.vmax;
+                    int32_t m = kInf;
+                    for (int32_t i = tid; i < nd; i += nthr) {
+                        const int32_t e = load_arr(arr, __ldcg(L + i), arr_shared);
+                        if (e >= H) m = min(m, e);
+                    }
+                    m = __reduce_min_sync(0xffffffffu, m);
+                    if ((tid & 31) == 0 && m < kInf) atomicMin(&s_def[3], m);
+                    __syncthreads();
+                    const int32_t lo = s_def[3];
+                    const int32_t Hn = lo < kInf - qa.horizon ? lo + qa.horizon : kInf;
+                    for (int32_t i = tid; i < nd; i += nthr) {
+                        const int32_t v = __ldcg(L + i);
+                        const int32_t e = load_arr(arr, v, arr_shared);
+                        if (e < H) continue;
+                        if (e < Hn) sp_next[atomicAdd(&s_def[2], 1)] = v;
+                        else K[atomicAdd(&s_def[1], 1)] = v;
+                    }
+                    __syncthreads();
+                    n_spill = s_def[2];
+                    H = Hn;
+                    dl ^= 1;
+                    if (tid == 0) s_def[0] = s_def[1];   // no thread reads [0] or [1] before this
+                    __syncthreads();
                 }
-                m = __reduce_min_sync(0xffffffffu, m);
-                if ((tid & 31) == 0 && m < kInf) atomicMin(&s_def[3], m);
-                __syncthreads();
-                const int32_t lo = s_def[3];
-                const int32_t Hn = lo < kInf - qa.horizon ? lo + qa.horizon : kInf;
-                for (int32_t i = tid; i < nd; i += nthr) {
-                    const int32_t v = __ldcg(L + i);
-                    const int32_t e = load_arr(arr, v, arr_shared);
-                    if (e < H) continue;
-                    if (e < Hn) sp_next[atomicAdd(&s_def[2], 1)] = v;
-                    else K[atomicAdd(&s_def[1], 1)] = v;
-                }
-                __syncthreads();
-                n_spill = s_def[2];
-                H = Hn;
-                dl ^= 1;
-                if (tid == 0) s_def[0] = s_def[1];   // no thread reads [0] or [1] before this
-                __syncthreads();
             }
         }
         const int32_t F = n_items + n_spill;
