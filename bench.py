@@ -61,8 +61,11 @@ BYTES = {"vertices": 20, "types": 28, "aps": 16, "relaxed": 12}
 # the 20 timed launches: 1,024 queries on the large network, 256 on the city network);
 # keyed by the kernel source hash, the kernel's name, the block size, the horizon and the
 # cluster width, so that another kernel or launch shape reports null until it is
-# profiled again.  Filled in from the captures of the current kernel.
-NCU_TRAFFIC_PER_QUERY = {}
+# profiled again.
+NCU_TRAFFIC_PER_QUERY = {
+    "large": ("7ed2d616fde77f66", "eat_cta_kernel", 512, 3600, 600, 14553038694 / 1024),
+    "city": ("7ed2d616fde77f66", "eat_cta_kernel", 1024, -1, 600, 135171853 / 256),
+}
 KERNEL_OF_MODE = {1: "eat_cta_kernel", 2: "eat_cluster_kernel", 3: "eat_async_kernel",
                   4: "eat_pair_kernel", 5: "eat_cta_kernel"}
 
