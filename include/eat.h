@@ -400,11 +400,12 @@ int eat_launch_shape(const eat_net *const *nets, int32_t n_nets, int32_t n,
  * If every buffer is device memory the call is asynchronous on `stream`.  If
  * any is host memory the call returns after the results are in arr_out: when
  * arr_out is page-locked host memory mapped for the device (cudaHostAlloc,
- * cudaHostRegister) and the arrivals fit in shared memory, the kernel writes
- * each query's row straight into arr_out as the query finishes (and reads
- * page-locked sources/times in place), so the transfer overlaps the other
- * queries; otherwise host buffers are staged through device memory with
- * copies before and after the launch.  Per-query round-cap failures are reported
+ * cudaHostRegister), the kernel writes each query's row into arr_out itself (and
+ * reads page-locked sources/times in place), so the transfer overlaps the other
+ * queries: as each query finishes, from shared memory or, for arrivals kept in a
+ * device row of the block (networks too large for shared memory), from that row;
+ * otherwise host buffers are staged through device memory with copies before and
+ * after the launch.  Per-query round-cap failures are reported
  * only through opts->status (the return value covers launch errors).
  * Errors: EAT_ERR_INVALID, EAT_ERR_WORKSPACE, EAT_ERR_NO_DEVICE, EAT_ERR_CUDA,
  * EAT_ERR_OOM.
@@ -622,10 +623,12 @@ void eat_server_destroy(eat_server *sv);
  *   - Limit: each persistent thread block needs 8 * n_stops bytes of the scratch
  *     (rounded up) for its frontier queue, plus n_stops / 4 bytes when the frontier
  *     bitmaps live in global memory (networks beyond about 900,000 stops), or
- *     16 * n_stops bytes in the paired mode (two queries per block); the round-free
- *     mode needs none.  So the network may have at most 2,000,000 stops, and on
- *     large networks fewer blocks run at once while the other queries wait in the
- *     same launch.  Larger networks are rejected with EAT_ERR_INVALID.
+ *     16 * n_stops bytes in the paired mode (two queries per block); with a
+ *     horizon, 16 * n_stops + n_stops / 8 bytes (the lists of waiting stops); the
+ *     round-free mode needs none.  So the network may have at most 2,000,000 stops
+ *     (about 1,000,000 with a horizon), and on large networks fewer blocks run at
+ *     once while the other queries wait in the same launch.  Larger networks are
+ *     rejected with EAT_ERR_INVALID.
  * Errors: EAT_ERR_INVALID (host buffers, network too large, bad options),
  * EAT_ERR_NO_DEVICE, EAT_ERR_CUDA.
  */

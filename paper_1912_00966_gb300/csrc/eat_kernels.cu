@@ -65,6 +65,24 @@ __device__ __forceinline__ int32_t load_arr(const int32_t *arr, int32_t i, bool 
     return __ldcg(arr + i);
 }
 
+// A converged query's row from its arrivals (shared memory, or a global row) to `out`
+// (device or page-locked host memory) by the block's threads: 16-byte loads and stores
+// when both start on a 16-byte boundary (a quarter of the transactions, which matters
+// most for rows written to host memory), else 4-byte ones.  The caller has passed a
+// barrier since the last write to `arr`.
+__device__ __forceinline__ void copy_row(int32_t *out, const int32_t *arr, int32_t V, bool shared,
+                                         int tid, int nthr) {
+    int32_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(arr)) & 15) == 0) {
+        const int32_t n4 = V >> 2;
+        int4 *const o4 = reinterpret_cast<int4 *>(out);
+        const int4 *const a4 = reinterpret_cast<const int4 *>(arr);
+        for (int32_t i = tid; i < n4; i += nthr) o4[i] = shared ? a4[i] : __ldcg(a4 + i);
+        done = n4 << 2;
+    }
+    for (int32_t i = done + tid; i < V; i += nthr) out[i] = shared ? arr[i] : __ldcg(arr + i);
+}
+
 // Index of the next query a persistent block takes: the work counter's next value,
 // through the start order when there is one (values >= n end the block's loop).
 __device__ __forceinline__ int32_t next_query(const QueryArgs &qa) {
@@ -429,7 +447,7 @@ eat_cta_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa) 
 
         if (arr_shared || qa.arr_rows) {
             __syncthreads();
-            for (int32_t i = tid; i < V; i += nthr) out[i] = load_arr(arr, i, arr_shared);
+            copy_row(out, arr, V, arr_shared, tid, nthr);
         }
         const int32_t q_status = !valid ? EAT_ERR_INVALID : (F > 0 ? EAT_ERR_NO_CONVERGENCE : EAT_OK);
         if (RING) {
@@ -567,7 +585,7 @@ eat_pair_kernel(const __grid_constant__ NetTable<1> nets, const QueryArgs qa) {
                 const int64_t off = qa.arr_off ? __ldg(qa.arr_off + q) : (int64_t)q * V;
                 int32_t *const out = qa.arr_out + off;
                 const int32_t *const a = smem + j * vpad;
-                for (int32_t i = tid; i < V; i += nthr) out[i] = load_arr(a, i, true);
+                copy_row(out, a, V, true, tid, nthr);
                 if (tid == 0) {
                     if (qa.status)
                         qa.status[q] = !vq[j] ? EAT_ERR_INVALID
@@ -906,8 +924,7 @@ eat_async_kernel(const __grid_constant__ NetTable<NETS> nets, const QueryArgs qa
         }
         __syncthreads();
 
-        if (arr_shared || qa.arr_rows)
-            for (int32_t i = tid; i < V; i += nthr) out[i] = load_arr(arr, i, arr_shared);
+        if (arr_shared || qa.arr_rows) copy_row(out, arr, V, arr_shared, tid, nthr);
         if (tid == 0 && qa.status)
             qa.status[q] = !valid ? EAT_ERR_INVALID : (s_err ? EAT_ERR_NO_CONVERGENCE : EAT_OK);
         if (qa.counters) {

@@ -133,6 +133,51 @@ def test_pinned_host_rows_written_in_place(eat, city, mode):
         assert np.array_equal(one.numpy(), want[i])
 
 
+@pytest.mark.parametrize("placement", [2, 3])
+def test_host_rows_written_by_the_kernel(eat, city, placement):
+    """Rows of queries whose arrivals live in a device row of the block are copied by the
+    block (16-byte words) into page-locked host memory as each query converges: 1,000
+    queries, so each block reuses its row several times; every row equals the oracle's,
+    in a batch whose buffers are all host memory and in one that starts from device
+    queries."""
+    q = synth.random_queries(city.tt, 1000, 0x7C + placement)
+    want = city.oracle_rows(q.source, q.t_s)
+    rows = torch.full((1000, city.V), -7, dtype=torch.int32).pin_memory()
+    eat.eat_query_batch(city.net, torch.as_tensor(q.source).pin_memory(),
+                        torch.as_tensor(q.t_s).pin_memory(), rows, placement=placement)
+    assert np.array_equal(rows.numpy(), want)
+    rows.fill_(-7)
+    eat.eat_query_batch(city.net, _dev(q.source), _dev(q.t_s), rows, placement=placement,
+                        block=256)
+    assert np.array_equal(rows.numpy(), want)
+
+
+def test_ragged_batch_into_host_rows(eat):
+    """Networks of uneven size, arrivals shared or in device rows per query, rows written
+    into one page-locked host buffer (row offsets not all 16-byte aligned)."""
+    import os
+    tts = synth.ragged_grids(10, seed_offset=3)
+    nets = [eat.eat_build(t.n_stops, t.u, t.v, t.dep, t.dur, device=0) for t in tts]
+    Q = 700
+    qs = synth.random_queries(tts, Q, 0x7E)
+    sizes = np.array([tts[i].n_stops for i in qs.net], np.int64)
+    offs = np.concatenate([[0], np.cumsum(sizes + 1)[:-1]]).astype(np.int64)   # odd gaps
+    out = torch.full((int(offs[-1] + sizes[-1]),), -7, dtype=torch.int32).pin_memory()
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    eat.eat_query_batch_multi(nets, i32(qs.net), i32(qs.source), i32(qs.t_s), out, offs)
+    flat = out.numpy()
+    for j, tt in enumerate(tts):
+        sel = np.nonzero(qs.net == j)[0]
+        if sel.size == 0:
+            continue
+        want = oracle.csa_many(oracle.SortedConnections(tt), qs.source[sel], qs.t_s[sel],
+                               os.cpu_count() or 8)[0]
+        for r, i in enumerate(sel):
+            assert np.array_equal(flat[offs[i]:offs[i] + tt.n_stops], want[r]), (j, i)
+    for n in nets:
+        n.close()
+
+
 @pytest.mark.parametrize("seed", range(30))
 def test_tiny_random_nets_all_sources(eat, seed):
     tt = synth.tiny_random(2 + seed % 13, 1 + (seed * 37) % 300, 500 + seed, t_max=300 + 50 * seed,
@@ -355,6 +400,15 @@ def test_large_network_all_rows(eat, large_tt, large_sc):
         bad = np.nonzero((got != want).any(axis=1))[0]
         assert bad.size == 0, (width, tune, opts, bad[:8])
         del out
+        if tune:
+            # the same batch from and into page-locked host memory (the end-to-end path:
+            # each block copies its converged rows into the host buffer)
+            host = torch.full((1024, tt.n_stops), -7, dtype=torch.int32).pin_memory()
+            eat.eat_query_batch(net, torch.as_tensor(q.source).pin_memory(),
+                                torch.as_tensor(q.t_s).pin_memory(), host)
+            bad = np.nonzero((host.numpy() != want).any(axis=1))[0]
+            assert bad.size == 0, ("host rows", bad[:8])
+            del host
         net.close()
     for i in (0, 511, 1023):
         assert oracle.certify(tt, int(q.source[i]), int(q.t_s[i]), want[i]) == (0, -1)
