@@ -63,8 +63,8 @@ BYTES = {"vertices": 20, "types": 28, "aps": 16, "relaxed": 12}
 # cluster width, so that another kernel or launch shape reports null until it is
 # profiled again.
 NCU_TRAFFIC_PER_QUERY = {
-    "large": ("7ed2d616fde77f66", "eat_cta_kernel", 512, 3600, 600, 14553038694 / 1024),
-    "city": ("7ed2d616fde77f66", "eat_cta_kernel", 1024, -1, 600, 135171853 / 256),
+    "large": ("2de258fb4eb0b1dc", "eat_cta_kernel", 512, 3600, 600, 14555841037 / 1024),
+    "city": ("2de258fb4eb0b1dc", "eat_cta_kernel", 1024, -1, 600, 135806746 / 256),
 }
 KERNEL_OF_MODE = {1: "eat_cta_kernel", 2: "eat_cluster_kernel", 3: "eat_async_kernel",
                   4: "eat_pair_kernel", 5: "eat_cta_kernel"}
