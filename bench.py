@@ -108,7 +108,8 @@ def run_ours_ragged(args):
     out = torch.empty(total, dtype=torch.int32, device="cuda")
     cnt = torch.zeros((n_steps, Q, 7), dtype=torch.int64, device="cuda")
     status = torch.zeros((n_steps, Q), dtype=torch.int32, device="cuda")
-    opts = dict(vwarp=args.vwarp, block=args.block, mode=args.mode, horizon=args.horizon)
+    opts = dict(vwarp=args.vwarp, block=args.block, mode=args.mode, horizon=args.horizon,
+                order=args.order)
     tuned = None
     if args.autotune and not (args.vwarp or args.block or args.mode or args.horizon):
         # Launch shape and start order chosen by the library's multi-network autotuner on
@@ -672,7 +673,8 @@ def run_ours(args):
     out = torch.empty(batch * V, dtype=torch.int32, device="cuda")
     cnt = torch.zeros((n_steps, batch, 7), dtype=torch.int64, device="cuda")
     status = torch.zeros((n_steps, batch), dtype=torch.int32, device="cuda")
-    opts = dict(vwarp=args.vwarp, block=args.block, mode=args.mode, horizon=args.horizon)
+    opts = dict(vwarp=args.vwarp, block=args.block, mode=args.mode, horizon=args.horizon,
+                order=args.order)
     tuned = None
     if args.autotune and not (args.vwarp or args.block or args.mode or args.horizon):
         # Launch shape chosen by the library's autotuner on a sample batch (setup, untimed).
@@ -884,6 +886,8 @@ def main():
     ap.add_argument("--horizon", type=int, default=0,
                     help="seconds; 0 the tuned value (else none), -1 none (every improved stop "
                          "expanded next round, Algorithms 4-5)")
+    ap.add_argument("--order", type=int, default=0,
+                    help="start order of a batch: 0 automatic, 1 by t_s, 2 as given")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--cluster-width", type=int, default=600,
