@@ -30,9 +30,9 @@
 // warps).
 //
 // Horizon (qa.horizon > 0, an option; not in the paper): Algorithms 4-5 expand every
-// improved stop in the next round, so a stop that an early round reaches with a late
-// arrival (by a path of few connections) is expanded, and its successors with it, again
-// each time a later round improves it.  With a horizon H a stop lowered to an arrival >= H is not queued but
+// improved stop in the next round, so a stop first reached late by a path of few
+// connections is expanded, and its successors with it, again each time a later round
+// improves it.  With a horizon H a stop lowered to an arrival >= H is not queued but
 // waits (once, in a per-block list with a bitmap); when no stop below H is left to
 // expand, waiting stops whose arrival has since dropped below H are dropped (they
 // were queued by that lowering), H moves to the earliest remaining arrival + horizon,
